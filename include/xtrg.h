@@ -1,0 +1,146 @@
+/*
+ * xtrg.h -- C ABI of the GB300 XTRG beta-doubling engine.
+ *
+ * The engine implements the hot path of the exponential thermal tensor
+ * renormalization group of arXiv:1801.00142:
+ *
+ *   rho(tau0) = sum_{k=0}^{Nc} (-tau0)^k H^k / k!           (Eq. RhoTau, Sec. II C)
+ *   rho_{n+1} = rho_n^T rho_n,  tau_{n+1} = 2 tau_n          (Eq. rho:scale2, Sec. II B;
+ *                                                            positivity-preserving form)
+ *
+ * where every MPO product is compressed back to bond dimension <= D* by the
+ * two-site variational product compression of App. D.1 (cost function
+ * Eq. MPO:prod, local solution Eq. LSEProd, environments and splitting of
+ * Fig. VMPO), followed by normalisation and the thermodynamic quantities of
+ * Eq. ThermalQuan (Sec. III A).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - MPO site tensor i is a dense real array W_i[Dl][d][d][Dr], row-major,
+ *   where W_i[l][s][t][r] is the coefficient of |s><t| (row spin s, column
+ *   spin t) between left bond l and right bond r.  bond_dims has L+1
+ *   entries with bond_dims[0] = bond_dims[L] = 1.  Only d = 2 is supported.
+ * - All host pointers passed in are read during the call and never retained:
+ *   inputs are copied, the caller keeps ownership of its arrays.
+ * - Device memory: the library allocates nothing on the device.  The caller
+ *   provides one device workspace of at least xtrg_workspace_bytes() bytes
+ *   (256-byte aligned); it is borrowed until xtrg_destroy and never freed by
+ *   the library.  The library allocates small host bookkeeping only.
+ * - Streams: every device operation is issued on the CUDA stream given to
+ *   xtrg_create (a cudaStream_t passed as void*; NULL = legacy default
+ *   stream).  Calls that return scalars or bond dimensions to the host
+ *   synchronise that stream before returning.
+ * - Errors: every call returns an xtrg_status; no exception or abort crosses
+ *   the ABI.  After a failure xtrg_last_error(ctx) holds a one-line message.
+ *   A context that returned XTRG_ECUDA should be destroyed.
+ * - Thread safety: a context must not be used from two threads at once.
+ */
+#ifndef XTRG_H
+#define XTRG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  XTRG_OK = 0,
+  XTRG_EINVAL = 1,   /* bad argument: shape, size, NULL, unsupported option   */
+  XTRG_ENOMEM = 2,   /* workspace too small                                   */
+  XTRG_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed           */
+  XTRG_ENUMERIC = 4, /* non-finite or non-positive norm/trace, SVD not converged */
+  XTRG_ETIMEOUT = 5  /* a bounded device-side wait ran out                    */
+} xtrg_status;
+
+/* Arithmetic of the environment and two-site contractions (the O(D^4 d^3)
+ * part).  Splitting, canonicalisation, normalisation and traces are FP64 in
+ * every mode. */
+typedef enum {
+  XTRG_FP64 = 0,      /* FP64 CUDA-core contractions                          */
+  XTRG_TF32X3 = 1,    /* tcgen05 tensor cores, 3-term split TF32, FP32 accumulate */
+  XTRG_BF16X3 = 2     /* tcgen05 tensor cores, 3-term split BF16, FP32 accumulate */
+} xtrg_precision;
+
+/* An MPO given by host arrays (see conventions above). */
+typedef struct {
+  int L;                      /* number of sites, >= 2                        */
+  int d;                      /* local dimension, must be 2                   */
+  const int* bond_dims;       /* L+1 entries, first and last = 1              */
+  const double* const* W;     /* L host pointers, W[i] has bond_dims[i]*d*d*bond_dims[i+1] doubles */
+} xtrg_mpo;
+
+typedef struct {
+  double tau0;          /* initial inverse temperature, > 0                   */
+  int order;            /* series order Nc of Eq. RhoTau, 1..16               */
+  int dstar;            /* bond dimension cap D*, 1..1024                      */
+  int sweeps;           /* full sweeps (L->R then R->L) per doubling, >= 1    */
+  int init_sweeps;      /* full sweeps per product in the initialisation      */
+  xtrg_precision prec;  /* contraction arithmetic for beta >= beta_switch     */
+  double beta_switch;   /* doublings that start below this beta run in FP64   */
+  double svd_rel_tol;   /* singular values <= svd_rel_tol * sigma_max are dropped (numerically zero) */
+} xtrg_config;
+
+typedef struct {
+  double beta;          /* inverse temperature of the current rho             */
+  double lnZ;           /* ln Tr rho(beta)                                    */
+  double f;             /* free energy per site, -lnZ / (N beta)              */
+  double u;             /* energy per site, Tr(H rho) / (N Tr rho)            */
+  double c;             /* specific heat per site, beta^2 (<H^2> - <H>^2) / N */
+  double lnZ2;          /* ln Z(2 beta) = ln ||rho(beta)||_F^2 (Sec. II B)    */
+  double trunc_err;     /* largest discarded weight of the last sweep          */
+  double herm_defect;   /* reserved, 0                                        */
+  int max_bond;         /* largest bond dimension of the current rho          */
+  int n_doublings;      /* doublings done since xtrg_init                     */
+} xtrg_obs;
+
+typedef struct xtrg_ctx xtrg_ctx;
+
+/* Bytes of device workspace a context for (H, cfg) needs; 0 on bad input. */
+size_t xtrg_workspace_bytes(const xtrg_mpo* H, const xtrg_config* cfg);
+
+/* Create a context for Hamiltonian MPO H (copied to the workspace).
+ * dev_workspace: device pointer, >= xtrg_workspace_bytes(H, cfg) bytes.
+ * cuda_stream: cudaStream_t as void*.  On success *out is a new context. */
+xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* H, const xtrg_config* cfg,
+                        void* dev_workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* rho <- rho(tau0) by the series of Eq. RhoTau in Horner form, each product
+ * H*Y compressed variationally (App. D.1), "+I" an exact direct sum; then
+ * normalised.  beta <- tau0. */
+xtrg_status xtrg_init(xtrg_ctx* ctx);
+
+/* One doubling: rho <- compress(rho^T rho) with cfg.sweeps full sweeps,
+ * normalised; beta <- 2 beta (Eq. rho:scale2). */
+xtrg_status xtrg_double(xtrg_ctx* ctx);
+
+/* *lnZ <- ln Tr rho(beta) (a logarithm: Z overflows FP64 for long chains). */
+xtrg_status xtrg_trace(xtrg_ctx* ctx, double* lnZ);
+
+/* Thermodynamics of Eq. ThermalQuan at the current beta. */
+xtrg_status xtrg_observables(xtrg_ctx* ctx, xtrg_obs* out);
+
+/* Copy the current normalised rho to host memory.  bond_dims gets L+1 ints;
+ * W[i] must hold bond_dims[i]*4*bond_dims[i+1] doubles (query the dims first
+ * with W == NULL).  *lnc gets ln c, rho(beta) = e^{lnc} * rho. */
+xtrg_status xtrg_get_state(xtrg_ctx* ctx, int* bond_dims, double* const* W, double* lnc,
+                           double* beta);
+
+/* Replace the current rho by a host MPO (any gauge), its log scale lnc and
+ * its beta.  Bonds must not exceed the context's capacity (D* + 1). */
+xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* rho, double lnc, double beta);
+
+/* Work counters since creation: flops of the contraction GEMMs (algorithmic,
+ * 2*M*N*K per GEMM) and of the FP64 splitting, and device time is not kept. */
+xtrg_status xtrg_counters(const xtrg_ctx* ctx, double* contraction_flops, double* split_flops,
+                          long long* two_site_updates);
+
+const char* xtrg_last_error(const xtrg_ctx* ctx);
+
+/* Free host bookkeeping.  The workspace stays the caller's. */
+void xtrg_destroy(xtrg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XTRG_H */

@@ -1,0 +1,179 @@
+"""ctypes binding of the C ABI declared in include/xtrg.h.
+
+Argument marshalling only: every step of the XTRG path runs in the CUDA
+library.  Importing this module loads ``libxtrg.so`` and fails loudly if it
+has not been built (there is no fallback implementation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxtrg.so")
+
+XTRG_OK, XTRG_EINVAL, XTRG_ENOMEM, XTRG_ECUDA, XTRG_ENUMERIC, XTRG_ETIMEOUT = range(6)
+XTRG_FP64, XTRG_TF32X3, XTRG_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": XTRG_FP64, "tf32x3": XTRG_TF32X3, "bf16x3": XTRG_BF16X3}
+STATUS_NAMES = {0: "XTRG_OK", 1: "XTRG_EINVAL", 2: "XTRG_ENOMEM", 3: "XTRG_ECUDA",
+                4: "XTRG_ENUMERIC", 5: "XTRG_ETIMEOUT"}
+
+# every exported symbol the header declares
+SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "xtrg_trace",
+           "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_counters",
+           "xtrg_last_error", "xtrg_destroy"]
+
+
+class xtrg_mpo(C.Structure):
+    _fields_ = [("L", C.c_int), ("d", C.c_int), ("bond_dims", C.POINTER(C.c_int)),
+                ("W", C.POINTER(C.POINTER(C.c_double)))]
+
+
+class xtrg_config(C.Structure):
+    _fields_ = [("tau0", C.c_double), ("order", C.c_int), ("dstar", C.c_int),
+                ("sweeps", C.c_int), ("init_sweeps", C.c_int), ("prec", C.c_int),
+                ("beta_switch", C.c_double), ("svd_rel_tol", C.c_double)]
+
+
+class xtrg_obs(C.Structure):
+    _fields_ = [("beta", C.c_double), ("lnZ", C.c_double), ("f", C.c_double),
+                ("u", C.c_double), ("c", C.c_double), ("lnZ2", C.c_double),
+                ("trunc_err", C.c_double), ("herm_defect", C.c_double),
+                ("max_bond", C.c_int), ("n_doublings", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class XtrgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.xtrg_workspace_bytes.restype = C.c_size_t
+    lib.xtrg_workspace_bytes.argtypes = [C.POINTER(xtrg_mpo), C.POINTER(xtrg_config)]
+    lib.xtrg_create.restype = C.c_int
+    lib.xtrg_create.argtypes = [C.POINTER(P), C.POINTER(xtrg_mpo), C.POINTER(xtrg_config), P,
+                                C.c_size_t, P]
+    for name in ("xtrg_init", "xtrg_double"):
+        getattr(lib, name).restype = C.c_int
+        getattr(lib, name).argtypes = [P]
+    lib.xtrg_trace.restype = C.c_int
+    lib.xtrg_trace.argtypes = [P, C.POINTER(C.c_double)]
+    lib.xtrg_observables.restype = C.c_int
+    lib.xtrg_observables.argtypes = [P, C.POINTER(xtrg_obs)]
+    lib.xtrg_get_state.restype = C.c_int
+    lib.xtrg_get_state.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.POINTER(C.c_double)),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.xtrg_set_state.restype = C.c_int
+    lib.xtrg_set_state.argtypes = [P, C.POINTER(xtrg_mpo), C.c_double, C.c_double]
+    lib.xtrg_counters.restype = C.c_int
+    lib.xtrg_counters.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_longlong)]
+    lib.xtrg_last_error.restype = C.c_char_p
+    lib.xtrg_last_error.argtypes = [P]
+    lib.xtrg_destroy.restype = None
+    lib.xtrg_destroy.argtypes = [P]
+    return lib
+
+
+LIB = _load()
+
+
+class MpoArgs:
+    """Keeps the ctypes views of a host MPO alive while a call uses them."""
+
+    def __init__(self, dims, sites):
+        self.dims = np.ascontiguousarray(dims, dtype=np.int32)
+        self.sites = [np.ascontiguousarray(w, dtype=np.float64) for w in sites]
+        L = len(self.sites)
+        self.ptrs = (C.POINTER(C.c_double) * L)(
+            *[w.ctypes.data_as(C.POINTER(C.c_double)) for w in self.sites])
+        self.struct = xtrg_mpo(L, 2, self.dims.ctypes.data_as(C.POINTER(C.c_int)), self.ptrs)
+
+
+def make_config(tau0, order, dstar, sweeps, init_sweeps=None, prec="fp64", beta_switch=0.0,
+                svd_rel_tol=1e-15):
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    return xtrg_config(float(tau0), int(order), int(dstar), int(sweeps),
+                       int(init_sweeps or sweeps), p, float(beta_switch), float(svd_rel_tol))
+
+
+def _check(ctx, status):
+    if status != XTRG_OK:
+        msg = LIB.xtrg_last_error(ctx).decode() if ctx else ""
+        raise XtrgError(status, msg)
+
+
+def xtrg_workspace_bytes(H: MpoArgs, cfg: xtrg_config) -> int:
+    return int(LIB.xtrg_workspace_bytes(C.byref(H.struct), C.byref(cfg)))
+
+
+def xtrg_create(H: MpoArgs, cfg: xtrg_config, dev_ptr: int, nbytes: int, stream: int):
+    ctx = C.c_void_p()
+    s = LIB.xtrg_create(C.byref(ctx), C.byref(H.struct), C.byref(cfg), C.c_void_p(dev_ptr),
+                        C.c_size_t(nbytes), C.c_void_p(stream))
+    if s != XTRG_OK:
+        raise XtrgError(s, "xtrg_create")
+    return ctx
+
+
+def xtrg_init(ctx):
+    _check(ctx, LIB.xtrg_init(ctx))
+
+
+def xtrg_double(ctx):
+    _check(ctx, LIB.xtrg_double(ctx))
+
+
+def xtrg_trace(ctx) -> float:
+    v = C.c_double()
+    _check(ctx, LIB.xtrg_trace(ctx, C.byref(v)))
+    return v.value
+
+
+def xtrg_observables(ctx) -> dict:
+    o = xtrg_obs()
+    _check(ctx, LIB.xtrg_observables(ctx, C.byref(o)))
+    return o.as_dict()
+
+
+def xtrg_get_state(ctx, L):
+    dims = np.zeros(L + 1, dtype=np.int32)
+    lnc, beta = C.c_double(), C.c_double()
+    _check(ctx, LIB.xtrg_get_state(ctx, dims.ctypes.data_as(C.POINTER(C.c_int)), None,
+                                   C.byref(lnc), C.byref(beta)))
+    sites = [np.empty((dims[i], 2, 2, dims[i + 1])) for i in range(L)]
+    ptrs = (C.POINTER(C.c_double) * L)(*[w.ctypes.data_as(C.POINTER(C.c_double)) for w in sites])
+    _check(ctx, LIB.xtrg_get_state(ctx, dims.ctypes.data_as(C.POINTER(C.c_int)), ptrs,
+                                   C.byref(lnc), C.byref(beta)))
+    return sites, lnc.value, beta.value
+
+
+def xtrg_set_state(ctx, sites, lnc, beta):
+    dims = [1] + [w.shape[3] for w in sites]
+    m = MpoArgs(dims, sites)
+    _check(ctx, LIB.xtrg_set_state(ctx, C.byref(m.struct), float(lnc), float(beta)))
+
+
+def xtrg_counters(ctx):
+    a, b, n = C.c_double(), C.c_double(), C.c_longlong()
+    _check(ctx, LIB.xtrg_counters(ctx, C.byref(a), C.byref(b), C.byref(n)))
+    return {"contraction_flops": a.value, "split_flops": b.value, "two_site_updates": n.value}
+
+
+def xtrg_last_error(ctx) -> str:
+    return LIB.xtrg_last_error(ctx).decode()
+
+
+def xtrg_destroy(ctx):
+    LIB.xtrg_destroy(ctx)

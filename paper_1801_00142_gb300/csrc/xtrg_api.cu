@@ -1,0 +1,661 @@
+// C ABI and host driver of the XTRG beta-doubling engine (declared in xtrg.h).
+//
+// The host drives the sweep; every arithmetic step runs in this library's
+// kernels on the caller's stream.  All device memory is carved from the
+// caller's workspace.
+//
+// Method (arXiv:1801.00142):
+//   init    rho(tau0) = sum_k (-tau0)^k H^k / k!       Eq. RhoTau (Sec. II C),
+//           Horner form Y <- I + (-tau0/k) H Y; each product compressed by the
+//           variational scheme of App. D.1 with the exact product as guess,
+//           "+I" an exact direct sum.
+//   double  rho <- compress(rho^T rho)                  Eq. rho:scale2 (Sec. II B)
+//   compress: right-canonical guess, right environments, then full sweeps
+//           (L->R, R->L) of two-site updates C_i C_{i+1} = C_E  (Eq. LSEProd)
+//           with C_E from the environments of Fig. VMPO(a,c) and the split of
+//           Fig. VMPO(d), keeping at most D* singular values.
+//   normalise by the centre's Frobenius norm, ln c_{n+1} = 2 ln c_n + ln s.
+//   observables: Eq. ThermalQuan (Sec. III A) from Tr rho, Tr(H rho), Tr(H^2 rho).
+//
+// Storage: an MPO site W[l][s][t][r] is row-major; environments at bond i are
+// stored [c][a][b] (c = bond of the compressed MPO C, a/b = bonds of the
+// factors A/B); the left half of C_E is stored [c][s][u][a'][b'] and the
+// right half [s'][u'][c''][a'][b'], so C_E = Lpart * Rpart^T is one GEMM.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/xtrg.h"
+#include "common.cuh"
+#include "mixed.cuh"
+
+namespace {
+
+struct DevMpo {
+  std::vector<int> dims;        // L+1 bond dimensions
+  std::vector<double*> site;    // L device slots
+  size_t slot;                  // capacity of each slot, in doubles
+};
+
+struct Plan {
+  int L, DH, cap, cap_fat, fat_bond;
+  size_t n_h, n_site, n_fat, n_pp, n_env, n_part, n_ce, n_svd, n_svd_cols, n_usbuf, n_obs;
+  size_t mixed_bytes;
+  size_t total;
+};
+
+constexpr size_t ALIGN = 256;
+inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
+  if (L < 2 || DH < 1 || cfg->dstar < 1 || cfg->dstar > 1024) return false;
+  p->L = L;
+  p->DH = DH;
+  p->cap = cfg->dstar + 1;
+  p->cap_fat = p->cap < 64 ? p->cap : 64;
+  p->fat_bond = DH * p->cap_fat;
+  const size_t cap = p->cap;
+  const size_t fb = p->fat_bond;
+  const size_t big = fb > cap ? fb : cap;
+  p->n_h = (size_t)DH * 4 * DH;
+  p->n_site = cap * 4 * cap;
+  p->n_fat = fb * 4 * fb;
+  p->n_pp = big * 4 * cap;
+  size_t dab = (cap > (size_t)DH ? cap : (size_t)DH) * cap;   // Da*Db bound
+  p->n_env = dab * cap;
+  p->n_part = 4 * cap * dab;
+  p->n_ce = 16 * cap * cap;
+  size_t s1 = 16 * cap * cap, s2 = 4 * cap * big;
+  p->n_svd = s1 > s2 ? s1 : s2;
+  p->n_svd_cols = (4 * cap > big ? 4 * cap : big);
+  p->n_usbuf = big * cap;
+  p->n_obs = (size_t)DH * DH * 4 * cap * 2;
+  p->mixed_bytes = (cfg->prec == XTRG_FP64) ? 0 : mixed_workspace_bytes(L, p->cap, DH);
+  size_t t = 0;
+  t += up((size_t)L * p->n_h * 8);          // H
+  t += up((size_t)L * 4 * 8);               // identity sites
+  t += 3 * up((size_t)L * p->n_site * 8);   // rho, C, Y
+  t += up((size_t)L * p->n_fat * 8);        // fat guess
+  t += 2 * up(p->n_pp * 8);                 // canonicalisation ping-pong
+  t += up((size_t)(L + 1) * p->n_env * 8);  // environments
+  t += 3 * up(p->n_part * 8);               // T1, Lpart, Rpart
+  t += up(p->n_ce * 8);                     // C_E
+  t += 2 * up(p->n_svd * 8) + up(p->n_svd_cols * 8) + up(p->n_svd_cols * 4) + 3 * ALIGN;
+  t += up(p->n_usbuf * 8);
+  t += 3 * up(p->n_obs * 8);
+  t += up(64 * 8);                          // scalars
+  t += up(p->mixed_bytes);
+  p->total = t;
+  return true;
+}
+
+}  // namespace
+
+struct xtrg_ctx {
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0, used = 0;
+  xtrg_config cfg{};
+  Plan plan{};
+  int L = 0, DH = 0, cap = 0;
+  DevMpo H, rho, C, Y, I, fat;
+  double* pp[2] = {nullptr, nullptr};
+  std::vector<double*> env;
+  double *T1 = nullptr, *Lp = nullptr, *Rp = nullptr, *CE = nullptr, *usbuf = nullptr;
+  double *ob[3] = {nullptr, nullptr, nullptr};
+  double* scal = nullptr;
+  SvdBuffers svd{};
+  MixedCtx* mixed = nullptr;
+  bool use_mixed = false;   // contraction arithmetic of the current product
+  double lnc = 0.0, beta = 0.0;
+  int nd = 0;
+  bool have_rho = false;
+  double last_trunc = 0.0;
+  double flops_contr = 0.0, flops_split = 0.0;
+  long long updates = 0;
+  std::string err;
+};
+
+namespace {
+
+xtrg_status fail(xtrg_ctx* c, xtrg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(x)                                                                               \
+  do {                                                                                      \
+    cudaError_t _e = (x);                                                                   \
+    if (_e != cudaSuccess)                                                                  \
+      return fail(ctx, XTRG_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #x,                  \
+                  cudaGetErrorString(_e));                                                  \
+  } while (0)
+#define TRY(x)                                                                              \
+  do {                                                                                      \
+    xtrg_status _s = (x);                                                                   \
+    if (_s != XTRG_OK) return _s;                                                           \
+  } while (0)
+
+char* carve(xtrg_ctx* c, size_t bytes) {
+  size_t b = up(bytes);
+  if (c->used + b > c->ws_bytes) return nullptr;
+  char* p = c->ws + c->used;
+  c->used += b;
+  return p;
+}
+
+bool carve_mpo(xtrg_ctx* c, DevMpo* m, size_t slot) {
+  m->slot = slot;
+  m->dims.assign(c->L + 1, 1);
+  m->site.resize(c->L);
+  double* base = (double*)carve(c, (size_t)c->L * slot * 8);
+  if (!base) return false;
+  for (int i = 0; i < c->L; ++i) m->site[i] = base + (size_t)i * slot;
+  return true;
+}
+
+size_t site_elems(const DevMpo& m, int i) { return (size_t)m.dims[i] * 4 * m.dims[i + 1]; }
+
+// ------------------------------------------------------------------ GEMMs
+xtrg_status gemm(xtrg_ctx* ctx, const GemmF64& g) {
+  ctx->flops_contr += 2.0 * g.M * (double)g.N * g.K * g.batch;
+  if (ctx->use_mixed) {
+    cudaError_t e = mixed_gemm(ctx->mixed, g, ctx->st);
+    if (e != cudaSuccess) return fail(ctx, XTRG_ECUDA, "mixed gemm: %s", cudaGetErrorString(e));
+    return XTRG_OK;
+  }
+  CK(gemm_f64(g, ctx->st));
+  return XTRG_OK;
+}
+
+// plain FP64 GEMM (bookkeeping contractions: canonicalisation, transfers)
+xtrg_status gemm64(xtrg_ctx* ctx, const GemmF64& g) {
+  CK(gemm_f64(g, ctx->st));
+  return XTRG_OK;
+}
+
+GemmF64 mk(int M, int N, int K, int batch, const double* A, Idx3 am, Idx3 ak, long long sab,
+           const double* B, Idx3 bk, Idx3 bn, long long sbb, double* C, Idx3 cm, Idx3 cn,
+           long long scb) {
+  GemmF64 g;
+  g.M = M; g.N = N; g.K = K; g.batch = batch;
+  g.A = A; g.am = am; g.ak = ak; g.sab = sab;
+  g.B = B; g.bk = bk; g.bn = bn; g.sbb = sbb;
+  g.C = C; g.cm = cm; g.cn = cn; g.scb = scb;
+  g.alpha = 1.0; g.beta = 0.0;
+  return g;
+}
+
+// ------------------------------------------------------- split (Fig. VMPO(d))
+xtrg_status split(xtrg_ctx* ctx, const double* M, int m, int n, int kcap, SplitMode mode,
+                  double* left, double* right, SvdResult* r) {
+  bool conv = true;
+  cudaError_t e = svd_split_f64(M, m, n, kcap, ctx->cfg.svd_rel_tol, mode, left, right, ctx->svd,
+                                ctx->st, r, &conv);
+  if (e != cudaSuccess) return fail(ctx, XTRG_ECUDA, "svd split %dx%d: %s", m, n, cudaGetErrorString(e));
+  if (!conv) return fail(ctx, XTRG_ENUMERIC, "Jacobi SVD of a %dx%d matrix did not converge", m, n);
+  if (!std::isfinite(r->sigma_max)) return fail(ctx, XTRG_ENUMERIC, "non-finite singular value");
+  int len = m > n ? m : n, nc = m > n ? n : m;
+  ctx->flops_split += (double)r->sweeps * nc * (nc - 1) / 2.0 * (6.0 * len + 4.0 * nc);
+  return XTRG_OK;
+}
+
+// Right-canonicalise the MPO given by (src_dims, src) into C: for i = L-1..1
+// the site is split by an SVD into (U Lambda) V^T, V^T is kept and U Lambda is
+// multiplied into site i-1.  Only numerically-zero directions are dropped.
+xtrg_status canonicalize(xtrg_ctx* ctx, const std::vector<int>& sdims,
+                         const std::vector<double*>& src, DevMpo& C) {
+  const int L = ctx->L;
+  const double* cur = src[L - 1];
+  int cl = sdims[L - 1], cr = 1;
+  C.dims[L] = 1;
+  for (int i = L - 1; i >= 1; --i) {
+    SvdResult r;
+    TRY(split(ctx, cur, cl, 4 * cr, ctx->cap, SPLIT_LEFT, ctx->usbuf, C.site[i], &r));
+    if (r.rank > ctx->cap)
+      return fail(ctx, XTRG_ENOMEM, "canonical bond at site %d exceeds capacity %d", i, ctx->cap);
+    C.dims[i] = r.k;
+    // site i-1 times (U Lambda): (l' * 4) x cl times cl x k
+    int lp = sdims[i - 1];
+    double* out = ctx->pp[i & 1];
+    GemmF64 g = mk(lp * 4, r.k, cl, 1, src[i - 1], idx_plain(cl), idx_plain(1), 0, ctx->usbuf,
+                   idx_plain(r.k), idx_plain(1), 0, out, idx_plain(r.k), idx_plain(1), 0);
+    TRY(gemm64(ctx, g));
+    cur = out;
+    cl = lp;
+    cr = r.k;
+  }
+  C.dims[0] = 1;
+  CK(cudaMemcpyAsync(C.site[0], cur, sizeof(double) * 4 * cr, cudaMemcpyDeviceToDevice, ctx->st));
+  return XTRG_OK;
+}
+
+// Left half of C_E at site i (Fig. VMPO(a,c), substeps 1-2):
+//   T1[c][b][t][s][a'] = sum_a V_L[c][a][b] A_i[a][t][s][a']
+//   Lp[c][s][u][a'][b'] = sum_{b,t} T1[c][b][t][s][a'] B_i[b][t][u][b']
+xtrg_status left_part(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, const DevMpo& C, int i,
+                      const double* VL) {
+  const int a = A.dims[i], a2 = A.dims[i + 1], b = B.dims[i], b2 = B.dims[i + 1], c = C.dims[i];
+  TRY(gemm(ctx, mk(b, 4 * a2, a, c, VL, idx_plain(1), idx_plain(b), (long long)a * b, A.site[i],
+                   idx_plain(4 * a2), idx_plain(1), 0, ctx->T1, idx_plain(4 * a2), idx_plain(1),
+                   (long long)b * 4 * a2)));
+  const long long ab2 = (long long)a2 * b2;
+  TRY(gemm(ctx, mk(2 * a2, 2 * b2, 2 * b, c, ctx->T1, idx_plain(1), idx_plain(2 * a2),
+                   (long long)b * 4 * a2, B.site[i], idx_plain(2 * b2), idx_plain(1), 0, ctx->Lp,
+                   idx_split2(a2, 2 * ab2, b2), idx_split2(b2, ab2, 1), 4 * ab2)));
+  return XTRG_OK;
+}
+
+// Right half of C_E at site j (mirror of the above):
+//   T1[c''][a'][t'][s'][b''] = sum_a'' A_j[a'][t'][s'][a''] V_R[c''][a''][b'']
+//   Rp[s'][u'][c''][a'][b'] = sum_{t',b''} T1[c''][a'][t'][s'][b''] B_j[b'][t'][u'][b'']
+xtrg_status right_part(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, const DevMpo& C, int j,
+                       const double* VR) {
+  const int a1 = A.dims[j], a2 = A.dims[j + 1], b1 = B.dims[j], b2 = B.dims[j + 1];
+  const int c2 = C.dims[j + 1];
+  TRY(gemm(ctx, mk(4 * a1, b2, a2, c2, A.site[j], idx_plain(a2), idx_plain(1), 0, VR,
+                   idx_plain(b2), idx_plain(1), (long long)a2 * b2, ctx->T1, idx_plain(b2),
+                   idx_plain(1), (long long)4 * a1 * b2)));
+  const long long ab1 = (long long)a1 * b1;
+  TRY(gemm(ctx, mk(2 * a1, 2 * b1, 2 * b2, c2, ctx->T1, idx_split2(2, 4LL * b2, b2),
+                   idx_split2(b2, 2LL * b2, 1), (long long)4 * a1 * b2, B.site[j],
+                   idx_split2(b2, 2LL * b2, 1), idx_split2(2, 4LL * b2, b2), 0, ctx->Rp,
+                   idx_split2(2, b1, 2LL * c2 * ab1), idx_split2(2, 1, (long long)c2 * ab1),
+                   ab1)));
+  return XTRG_OK;
+}
+
+// V_L[i+1][c'][a'][b'] = sum_{c,s,u} C_i[c][s][u][c'] Lp[c][s][u][a'][b']   (substep 3)
+xtrg_status left_env(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, const DevMpo& C, int i,
+                     double* out) {
+  const int k = C.dims[i + 1], c = C.dims[i];
+  const long long ab2 = (long long)A.dims[i + 1] * B.dims[i + 1];
+  return gemm(ctx, mk(k, (int)ab2, 4 * c, 1, C.site[i], idx_plain(1), idx_plain(k), 0, ctx->Lp,
+                      idx_plain(ab2), idx_plain(1), 0, out, idx_plain(ab2), idx_plain(1), 0));
+}
+
+// V_R[j][c'][a'][b'] = sum_{s',u',c''} C_j[c'][s'][u'][c''] Rp[s'][u'][c''][a'][b']
+xtrg_status right_env(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, const DevMpo& C, int j,
+                      double* out) {
+  const int k = C.dims[j], c2 = C.dims[j + 1];
+  const long long ab1 = (long long)A.dims[j] * B.dims[j];
+  return gemm(ctx, mk(k, (int)ab1, 4 * c2, 1, C.site[j], idx_plain(4 * c2), idx_plain(1), 0,
+                      ctx->Rp, idx_plain(ab1), idx_plain(1), 0, out, idx_plain(ab1), idx_plain(1),
+                      0));
+}
+
+// Variational compression of A^T B into C (App. D.1).  C holds the guess,
+// already right-canonical; on return C is the compressed MPO with its
+// orthogonality centre at site 0.
+xtrg_status compress(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, DevMpo& C, int dstar,
+                     int sweeps) {
+  const int L = ctx->L;
+  const int kcap = dstar < ctx->cap ? dstar : ctx->cap;
+  CK(dev_fill(ctx->env[0], 1.0, 1, ctx->st));
+  CK(dev_fill(ctx->env[L], 1.0, 1, ctx->st));
+  for (int j = L - 1; j >= 1; --j) {
+    TRY(right_part(ctx, A, B, C, j, ctx->env[j + 1]));
+    TRY(right_env(ctx, A, B, C, j, ctx->env[j]));
+  }
+  double maxdisc = 0.0;
+  for (int s = 0; s < sweeps; ++s) {
+    const bool last = s == sweeps - 1;
+    for (int dir = 0; dir < 2; ++dir) {
+      for (int step = 0; step < L - 1; ++step) {
+        const int i = dir == 0 ? step : L - 2 - step;
+        TRY(left_part(ctx, A, B, C, i, ctx->env[i]));
+        TRY(right_part(ctx, A, B, C, i + 1, ctx->env[i + 2]));
+        const int m = 4 * C.dims[i], n = 4 * C.dims[i + 2];
+        const long long K = (long long)A.dims[i + 1] * B.dims[i + 1];
+        TRY(gemm(ctx, mk(m, n, (int)K, 1, ctx->Lp, idx_plain(K), idx_plain(1), 0, ctx->Rp,
+                         idx_plain(1), idx_plain(K), 0, ctx->CE, idx_plain(n), idx_plain(1), 0)));
+        SvdResult r;
+        TRY(split(ctx, ctx->CE, m, n, kcap, dir == 0 ? SPLIT_RIGHT : SPLIT_LEFT, C.site[i],
+                  C.site[i + 1], &r));
+        C.dims[i + 1] = r.k;
+        if (last && r.discarded > maxdisc) maxdisc = r.discarded;
+        if (dir == 0) TRY(left_env(ctx, A, B, C, i, ctx->env[i + 1]));
+        else TRY(right_env(ctx, A, B, C, i + 1, ctx->env[i + 1]));
+        ctx->updates++;
+      }
+    }
+  }
+  ctx->last_trunc = maxdisc;
+  return XTRG_OK;
+}
+
+// ||C_0||_F for the centre site; C_0 /= s.  Returns ln s.
+xtrg_status normalize(xtrg_ctx* ctx, DevMpo& C, double* lns) {
+  const long long n = (long long)site_elems(C, 0);
+  CK(dev_sumsq(C.site[0], n, ctx->scal, ctx->st));
+  double ss = 0.0;
+  CK(cudaMemcpyAsync(&ss, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (!(ss > 0.0) || !std::isfinite(ss))
+    return fail(ctx, XTRG_ENUMERIC, "norm of the compressed MPO is %g", ss);
+  const double s = std::sqrt(ss);
+  CK(dev_scale(C.site[0], 1.0 / s, n, ctx->st));
+  *lns = std::log(s);
+  return XTRG_OK;
+}
+
+bool mixed_for_beta(const xtrg_ctx* ctx, double beta) {
+  return ctx->cfg.prec != XTRG_FP64 && ctx->mixed && beta >= ctx->cfg.beta_switch;
+}
+
+// ------------------------------------------------------------ transfers
+// Tr rho, Tr(H rho), Tr(H^2 rho) by left-to-right transfer contractions.
+xtrg_status traces(xtrg_ctx* ctx, bool want_h, double out[3]) {
+  const int L = ctx->L;
+  const DevMpo& R = ctx->rho;
+  const DevMpo& H = ctx->H;
+  double* v[2] = {ctx->ob[0], ctx->ob[1]};
+  // Tr rho: v'[r'] = sum_{r,s} v[r] rho[r][s][s][r']
+  CK(dev_fill(v[0], 1.0, 1, ctx->st));
+  for (int i = 0; i < L; ++i) {
+    const int l = R.dims[i], r = R.dims[i + 1];
+    TRY(gemm64(ctx, mk(1, r, 2 * l, 1, v[i & 1], idx_plain(0), idx_split2(2, 1, 0), 0, R.site[i],
+                       idx_split2(2, 4LL * r, 3LL * r), idx_plain(1), 0, v[(i + 1) & 1],
+                       idx_plain(0), idx_plain(1), 0)));
+  }
+  CK(cudaMemcpyAsync(&out[0], v[L & 1], sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  out[1] = out[2] = 0.0;
+  if (want_h) {
+    // Tr(H rho): E'[h'][r'] = sum H[h][s][t][h'] E[h][r] rho[r][t][s][r']
+    double* E[2] = {ctx->ob[0], ctx->ob[1]};
+    double* T = ctx->ob[2];
+    CK(dev_fill(E[0], 1.0, 1, ctx->st));
+    for (int i = 0; i < L; ++i) {
+      const int l = R.dims[i], r = R.dims[i + 1], hl = H.dims[i], hr = H.dims[i + 1];
+      TRY(gemm64(ctx, mk(hl, 4 * r, l, 1, E[i & 1], idx_plain(l), idx_plain(1), 0, R.site[i],
+                         idx_plain(4 * r), idx_plain(1), 0, T, idx_plain(4 * r), idx_plain(1), 0)));
+      TRY(gemm64(ctx, mk(hr, r, 4 * hl, 1, H.site[i], idx_plain(1), idx_plain(hr), 0, T,
+                         idx_split3(2, 2, 4LL * r, r, 2LL * r), idx_plain(1), 0, E[(i + 1) & 1],
+                         idx_plain(r), idx_plain(1), 0)));
+    }
+    CK(cudaMemcpyAsync(&out[1], E[L & 1], sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    // Tr(H H rho): E'[h1'][h2'][r'] = sum E[h1][h2][r] H[h1][s][t][h1'] H[h2][t][v][h2'] rho[r][v][s][r']
+    double* T1 = ctx->ob[2];
+    double* T2 = ctx->ob[0];
+    double* Ea = ctx->ob[1];
+    CK(dev_fill(Ea, 1.0, 1, ctx->st));
+    for (int i = 0; i < L; ++i) {
+      const int l = R.dims[i], r = R.dims[i + 1], hl = H.dims[i], hr = H.dims[i + 1];
+      TRY(gemm64(ctx, mk(hl * hl, 4 * r, l, 1, Ea, idx_plain(l), idx_plain(1), 0, R.site[i],
+                         idx_plain(4 * r), idx_plain(1), 0, T1, idx_plain(4 * r), idx_plain(1), 0)));
+      TRY(gemm64(ctx, mk(hl * 2 * r, 2 * hr, 2 * hl, 1, T1, idx_split3(2, r, 4LL * r, 2LL * r, 1),
+                         idx_split2(2, (long long)hl * 4 * r, r), 0, H.site[i],
+                         idx_plain(2 * hr), idx_plain(1), 0, T2, idx_plain(2 * hr), idx_plain(1),
+                         0)));
+      TRY(gemm64(ctx, mk(hr, r, 4 * hl, hr, H.site[i], idx_plain(1), idx_plain(hr), 0, T2,
+                         idx_split3(2, 2, 2LL * r * 2 * hr, hr, (long long)r * 2 * hr),
+                         idx_plain(2 * hr), 1, Ea, idx_plain(r), idx_plain(1), (long long)hr * r)));
+    }
+    CK(cudaMemcpyAsync(&out[2], Ea, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return XTRG_OK;
+}
+
+xtrg_status check_mpo(const xtrg_mpo* m, int cap_bond) {
+  if (!m || m->L < 2 || m->d != 2 || !m->bond_dims || !m->W) return XTRG_EINVAL;
+  if (m->bond_dims[0] != 1 || m->bond_dims[m->L] != 1) return XTRG_EINVAL;
+  for (int i = 0; i <= m->L; ++i)
+    if (m->bond_dims[i] < 1 || m->bond_dims[i] > cap_bond) return XTRG_EINVAL;
+  for (int i = 0; i < m->L; ++i)
+    if (!m->W[i]) return XTRG_EINVAL;
+  return XTRG_OK;
+}
+
+int max_bond(const xtrg_mpo* m) {
+  int mx = 1;
+  for (int i = 0; i <= m->L; ++i) mx = m->bond_dims[i] > mx ? m->bond_dims[i] : mx;
+  return mx;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" size_t xtrg_workspace_bytes(const xtrg_mpo* H, const xtrg_config* cfg) {
+  if (!cfg || check_mpo(H, 1 << 20) != XTRG_OK) return 0;
+  Plan p;
+  if (!plan_sizes(H->L, max_bond(H), cfg, &p)) return 0;
+  return p.total;
+}
+
+extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtrg_config* cfg,
+                                   void* dev_workspace, size_t workspace_bytes, void* cuda_stream) {
+  if (!out) return XTRG_EINVAL;
+  *out = nullptr;
+  if (!cfg || check_mpo(Hm, 1 << 20) != XTRG_OK) return XTRG_EINVAL;
+  if (!(cfg->tau0 > 0.0) || cfg->order < 1 || cfg->order > 16 || cfg->sweeps < 1 ||
+      cfg->init_sweeps < 1 || cfg->dstar < 1 || cfg->dstar > 1024 || !(cfg->svd_rel_tol >= 0.0) ||
+      (int)cfg->prec < 0 || (int)cfg->prec > 2)
+    return XTRG_EINVAL;
+  if (!dev_workspace || ((uintptr_t)dev_workspace % ALIGN) != 0) return XTRG_EINVAL;
+  Plan p;
+  if (!plan_sizes(Hm->L, max_bond(Hm), cfg, &p)) return XTRG_EINVAL;
+  if (workspace_bytes < p.total) return XTRG_ENOMEM;
+  xtrg_ctx* ctx = new xtrg_ctx();
+  ctx->st = (cudaStream_t)cuda_stream;
+  ctx->ws = (char*)dev_workspace;
+  ctx->ws_bytes = workspace_bytes;
+  ctx->cfg = *cfg;
+  ctx->plan = p;
+  ctx->L = Hm->L;
+  ctx->DH = p.DH;
+  ctx->cap = p.cap;
+  bool ok = carve_mpo(ctx, &ctx->H, p.n_h) && carve_mpo(ctx, &ctx->I, 4) &&
+            carve_mpo(ctx, &ctx->rho, p.n_site) && carve_mpo(ctx, &ctx->C, p.n_site) &&
+            carve_mpo(ctx, &ctx->Y, p.n_site) && carve_mpo(ctx, &ctx->fat, p.n_fat);
+  ctx->pp[0] = (double*)carve(ctx, p.n_pp * 8);
+  ctx->pp[1] = (double*)carve(ctx, p.n_pp * 8);
+  double* envbase = (double*)carve(ctx, (size_t)(ctx->L + 1) * p.n_env * 8);
+  ctx->T1 = (double*)carve(ctx, p.n_part * 8);
+  ctx->Lp = (double*)carve(ctx, p.n_part * 8);
+  ctx->Rp = (double*)carve(ctx, p.n_part * 8);
+  ctx->CE = (double*)carve(ctx, p.n_ce * 8);
+  ctx->svd.W = (double*)carve(ctx, p.n_svd * 8);
+  ctx->svd.V = (double*)carve(ctx, p.n_svd * 8);
+  ctx->svd.sig = (double*)carve(ctx, p.n_svd_cols * 8);
+  ctx->svd.perm = (int*)carve(ctx, p.n_svd_cols * 4);
+  ctx->svd.counter = (int*)carve(ctx, 16);
+  ctx->svd.kept = (int*)carve(ctx, 16);
+  ctx->svd.stats = (double*)carve(ctx, 64);
+  ctx->svd.max_elems = p.n_svd;
+  ctx->svd.max_cols = (int)p.n_svd_cols;
+  ctx->usbuf = (double*)carve(ctx, p.n_usbuf * 8);
+  for (int i = 0; i < 3; ++i) ctx->ob[i] = (double*)carve(ctx, p.n_obs * 8);
+  ctx->scal = (double*)carve(ctx, 64 * 8);
+  ok = ok && envbase && ctx->pp[0] && ctx->pp[1] && ctx->T1 && ctx->Lp && ctx->Rp && ctx->CE &&
+       ctx->svd.W && ctx->svd.V && ctx->svd.sig && ctx->svd.perm && ctx->svd.counter &&
+       ctx->svd.kept && ctx->svd.stats && ctx->usbuf && ctx->ob[0] && ctx->ob[1] && ctx->ob[2] &&
+       ctx->scal;
+  if (ok && p.mixed_bytes) {
+    char* mb = carve(ctx, p.mixed_bytes);
+    ok = mb && mixed_create(&ctx->mixed, mb, p.mixed_bytes, ctx->L, ctx->cap, ctx->DH) == cudaSuccess;
+  }
+  if (!ok) {
+    delete ctx;
+    return XTRG_ENOMEM;
+  }
+  ctx->env.resize(ctx->L + 1);
+  for (int i = 0; i <= ctx->L; ++i) ctx->env[i] = envbase + (size_t)i * p.n_env;
+  // Hamiltonian and identity sites
+  for (int i = 0; i <= ctx->L; ++i) ctx->H.dims[i] = Hm->bond_dims[i];
+  for (int i = 0; i < ctx->L; ++i) {
+    cudaError_t e = cudaMemcpyAsync(ctx->H.site[i], Hm->W[i], sizeof(double) * site_elems(ctx->H, i),
+                                    cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) e = dev_identity_site(ctx->I.site[i], ctx->st);
+    if (e != cudaSuccess) {
+      delete ctx;
+      return XTRG_ECUDA;
+    }
+  }
+  if (cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+    delete ctx;
+    return XTRG_ECUDA;
+  }
+  *out = ctx;
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_init(xtrg_ctx* ctx) {
+  if (!ctx) return XTRG_EINVAL;
+  const int L = ctx->L;
+  ctx->use_mixed = false;  // the series initialisation always runs in FP64
+  // Y = I
+  for (int i = 0; i <= L; ++i) ctx->Y.dims[i] = 1;
+  for (int i = 0; i < L; ++i) CK(dev_identity_site(ctx->Y.site[i], ctx->st));
+  for (int k = ctx->cfg.order; k >= 1; --k) {
+    // guess: the exact product H^T Y with fused bonds
+    for (int i = 0; i <= L; ++i) {
+      if (ctx->Y.dims[i] > ctx->plan.cap_fat)
+        return fail(ctx, XTRG_ENOMEM, "series term bond %d exceeds the initial-guess capacity %d",
+                    ctx->Y.dims[i], ctx->plan.cap_fat);
+      ctx->fat.dims[i] = ctx->H.dims[i] * ctx->Y.dims[i];
+    }
+    for (int i = 0; i < L; ++i)
+      CK(mpo_exact_product(ctx->H.site[i], ctx->H.dims[i], ctx->H.dims[i + 1], ctx->Y.site[i],
+                           ctx->Y.dims[i], ctx->Y.dims[i + 1], ctx->fat.site[i], ctx->st));
+    TRY(canonicalize(ctx, ctx->fat.dims, ctx->fat.site, ctx->C));
+    TRY(compress(ctx, ctx->H, ctx->Y, ctx->C, ctx->cfg.dstar, ctx->cfg.init_sweeps));
+    // Y <- I + (-tau0/k) * (H Y)
+    const double alpha = -ctx->cfg.tau0 / k;
+    std::vector<int> nd(L + 1, 1);
+    for (int i = 1; i < L; ++i) nd[i] = ctx->C.dims[i] + 1;
+    for (int i = 0; i < L; ++i)
+      CK(mpo_direct_sum_site(ctx->C.site[i], ctx->C.dims[i], ctx->C.dims[i + 1], alpha,
+                             ctx->I.site[i], 1, 1, i, L, ctx->Y.site[i], ctx->st));
+    ctx->Y.dims = nd;
+  }
+  TRY(canonicalize(ctx, ctx->Y.dims, ctx->Y.site, ctx->C));
+  double lns = 0.0;
+  TRY(normalize(ctx, ctx->C, &lns));
+  std::swap(ctx->rho, ctx->C);
+  ctx->lnc = lns;
+  ctx->beta = ctx->cfg.tau0;
+  ctx->nd = 0;
+  ctx->have_rho = true;
+  ctx->last_trunc = 0.0;
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_double(xtrg_ctx* ctx) {
+  if (!ctx) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "xtrg_double before xtrg_init");
+  ctx->use_mixed = mixed_for_beta(ctx, ctx->beta);
+  if (ctx->use_mixed) {
+    cudaError_t e = mixed_prepare(ctx->mixed, ctx->rho.dims.data(), ctx->rho.site.data(), ctx->st);
+    if (e != cudaSuccess) return fail(ctx, XTRG_ECUDA, "mixed prepare: %s", cudaGetErrorString(e));
+  }
+  TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, ctx->C));
+  xtrg_status s = compress(ctx, ctx->rho, ctx->rho, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps);
+  ctx->use_mixed = false;
+  if (s != XTRG_OK) return s;
+  double lns = 0.0;
+  TRY(normalize(ctx, ctx->C, &lns));
+  std::swap(ctx->rho, ctx->C);
+  ctx->lnc = 2.0 * ctx->lnc + lns;
+  ctx->beta *= 2.0;
+  ctx->nd++;
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_trace(xtrg_ctx* ctx, double* lnZ) {
+  if (!ctx || !lnZ) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "no state");
+  double t[3];
+  TRY(traces(ctx, false, t));
+  if (!(t[0] > 0.0) || !std::isfinite(t[0]))
+    return fail(ctx, XTRG_ENUMERIC, "Tr rho = %g is not positive", t[0]);
+  *lnZ = ctx->lnc + std::log(t[0]);
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_observables(xtrg_ctx* ctx, xtrg_obs* o) {
+  if (!ctx || !o) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "no state");
+  double t[3];
+  TRY(traces(ctx, true, t));
+  if (!(t[0] > 0.0) || !std::isfinite(t[0]) || !std::isfinite(t[1]) || !std::isfinite(t[2]))
+    return fail(ctx, XTRG_ENUMERIC, "traces not finite/positive: %g %g %g", t[0], t[1], t[2]);
+  const double N = ctx->L, b = ctx->beta;
+  const double e1 = t[1] / t[0], e2 = t[2] / t[0];
+  memset(o, 0, sizeof *o);
+  o->beta = b;
+  o->lnZ = ctx->lnc + std::log(t[0]);
+  o->f = -o->lnZ / (N * b);
+  o->u = e1 / N;
+  o->c = b * b * (e2 - e1 * e1) / N;
+  // the stored rho is normalised, ||rho||_F = 1, so Z(2 beta) = e^{2 ln c}
+  o->lnZ2 = 2.0 * ctx->lnc;
+  o->trunc_err = ctx->last_trunc;
+  o->herm_defect = 0.0;
+  int mx = 1;
+  for (int d : ctx->rho.dims) mx = d > mx ? d : mx;
+  o->max_bond = mx;
+  o->n_doublings = ctx->nd;
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_get_state(xtrg_ctx* ctx, int* bond_dims, double* const* W, double* lnc,
+                                      double* beta) {
+  if (!ctx || !bond_dims) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "no state");
+  for (int i = 0; i <= ctx->L; ++i) bond_dims[i] = ctx->rho.dims[i];
+  if (lnc) *lnc = ctx->lnc;
+  if (beta) *beta = ctx->beta;
+  if (W) {
+    for (int i = 0; i < ctx->L; ++i) {
+      if (!W[i]) return fail(ctx, XTRG_EINVAL, "W[%d] is NULL", i);
+      CK(cudaMemcpyAsync(W[i], ctx->rho.site[i], sizeof(double) * site_elems(ctx->rho, i),
+                         cudaMemcpyDeviceToHost, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* r, double lnc, double beta) {
+  if (!ctx) return XTRG_EINVAL;
+  if (check_mpo(r, ctx->cap) != XTRG_OK || r->L != ctx->L)
+    return fail(ctx, XTRG_EINVAL, "state MPO has the wrong length or a bond above %d", ctx->cap);
+  if (!(beta > 0.0) || !std::isfinite(lnc)) return fail(ctx, XTRG_EINVAL, "bad beta or lnc");
+  for (int i = 0; i <= ctx->L; ++i) ctx->rho.dims[i] = r->bond_dims[i];
+  for (int i = 0; i < ctx->L; ++i)
+    CK(cudaMemcpyAsync(ctx->rho.site[i], r->W[i], sizeof(double) * site_elems(ctx->rho, i),
+                       cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->lnc = lnc;
+  ctx->beta = beta;
+  ctx->have_rho = true;
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_counters(const xtrg_ctx* ctx, double* cf, double* sf, long long* upd) {
+  if (!ctx) return XTRG_EINVAL;
+  if (cf) *cf = ctx->flops_contr;
+  if (sf) *sf = ctx->flops_split;
+  if (upd) *upd = ctx->updates;
+  return XTRG_OK;
+}
+
+extern "C" const char* xtrg_last_error(const xtrg_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" void xtrg_destroy(xtrg_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->mixed) mixed_destroy(ctx->mixed);
+  delete ctx;
+}

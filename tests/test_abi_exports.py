@@ -1,0 +1,66 @@
+"""CPU checks of the C ABI: the library loads and exports every function the
+header declares, and the host-side argument checks reject bad input without
+touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "xtrg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(xtrg_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_00142_gb300.build import build
+    build()
+    from paper_1801_00142_gb300 import _lib
+    return _lib
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 11
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    assert sorted(lib.SYMBOLS) == names
+
+
+def test_workspace_bytes_and_input_checks(lib):
+    from paper_1801_00142_gb300.hamiltonians import xxz_chain
+    dims, sites = xxz_chain(8)
+    H = lib.MpoArgs(dims, sites)
+    cfg = lib.make_config(2 ** -10, 4, 256, 4)
+    n = lib.xtrg_workspace_bytes(H, cfg)
+    assert n > 0
+    # larger D* needs more memory; bad configs give 0 bytes
+    assert lib.xtrg_workspace_bytes(H, lib.make_config(2 ** -10, 4, 512, 4)) > n
+    assert lib.xtrg_workspace_bytes(H, lib.make_config(2 ** -10, 4, 0, 4)) == 0
+    bad = lib.MpoArgs([2] + dims[1:], sites)
+    assert lib.xtrg_workspace_bytes(bad, cfg) == 0
+    # create rejects a NULL workspace before any device call
+    with pytest.raises(lib.XtrgError) as e:
+        lib.xtrg_create(H, cfg, 0, n, 0)
+    assert e.value.status == lib.XTRG_EINVAL
+    # and a workspace that is too small
+    with pytest.raises(lib.XtrgError) as e:
+        lib.xtrg_create(H, cfg, 256, n - 1024, 0)
+    assert e.value.status == lib.XTRG_ENOMEM
+
+
+def test_hamiltonian_builder_is_the_xxz_chain(lib):
+    import numpy as np
+
+    from oracle import hamiltonian as oh
+    from paper_1801_00142_gb300.hamiltonians import xxz_chain
+    for L, D in ((2, 1.0), (5, 0.35), (7, 1.3)):
+        dims, sites = xxz_chain(L, 1.0, D)
+        assert dims[0] == dims[-1] == 1 and all(d == 5 for d in dims[1:-1])
+        assert np.abs(oh.mpo_to_dense(sites) - oh.dense_xxz(L, 1.0, D)).max() < 1e-14

@@ -1,0 +1,136 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Observables are gauge invariant, so runs are compared per beta on ln Z, f, u,
+c_V; states are compared through their dense matrices (small L) or through
+bond dimensions and traces.  The FP64 path must agree with the oracle to the
+accumulated-rounding level (the oracle itself agrees with ED to ~1e-11), so
+the bars are |d lnZ| <= 1e-10 max(1, |lnZ|), |du| <= 1e-10, |dc| <= 1e-9.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def eng_cls():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_00142_gb300.build import build
+    build()
+    from paper_1801_00142_gb300.engine import XTRG
+    return XTRG
+
+
+def golden(name):
+    with open(os.path.join(HERE, "golden", f"oracle_{name}.json")) as f:
+        return json.load(f)
+
+
+def compare_rows(gpu, ref, tol_lnz=1e-10, tol_u=1e-10, tol_c=1e-9):
+    assert len(gpu) == len(ref)
+    for g, o in zip(gpu, ref):
+        assert abs(g["beta"] - o["beta"]) < 1e-14 * o["beta"]
+        assert abs(g["lnZ"] - o["lnZ"]) <= tol_lnz * max(1.0, abs(o["lnZ"])), (o["beta"], g["lnZ"], o["lnZ"])
+        assert abs(g["u"] - o["u"]) <= tol_u, (o["beta"], g["u"], o["u"])
+        assert abs(g["c"] - o["c"]) <= tol_c, (o["beta"], g["c"], o["c"])
+
+
+@pytest.mark.parametrize("name", ["xxx_L4", "xx_L6", "xxz_L6_trunc", "xxx_L10_trunc"])
+def test_small_cases_match_oracle(eng_cls, name):
+    gd = golden(name)
+    w = gd["workload"]
+    eng = eng_cls.xxz(w["L"], w["J"], w["Delta"], tau0=w["tau0"], dstar=w["dstar"],
+                      sweeps=w["sweeps"], order=w["order"], init_sweeps=w["init_sweeps"],
+                      svd_rel_tol=w["svd_rel_tol"])
+    rows = eng.run(w["n_doublings"])
+    compare_rows(rows, gd["rows"])
+    for g, o in zip(rows, gd["rows"]):
+        assert g["max_bond"] == max(o["bond_dims"])
+
+
+def test_untruncated_L8_matches_exact_diagonalisation(eng_cls):
+    from oracle import exact as ex
+    from oracle import hamiltonian as oh
+    gd = golden("xxz_L8_D256_fp64")
+    w = gd["workload"]
+    eng = eng_cls.xxz(w["L"], w["J"], w["Delta"], tau0=w["tau0"], dstar=w["dstar"],
+                      sweeps=w["sweeps"], order=w["order"])
+    rows = eng.run(w["n_doublings"])
+    compare_rows(rows, gd["rows"])
+    E = ex.ed_spectrum(oh.dense_xxz(w["L"], w["J"], w["Delta"]))
+    for g in rows:
+        e = ex.ed_thermo(E, g["beta"], w["L"])
+        assert abs(g["f"] - e["f"]) <= 1e-10 * abs(e["f"])
+        assert abs(g["u"] - e["u"]) <= 1e-10
+        assert abs(g["c"] - e["c"]) <= 1e-9
+
+
+def test_init_state_matches_oracle_densely(eng_cls):
+    from oracle import hamiltonian as oh
+    from oracle import xtrg as ox
+    L, D, tau0 = 6, 0.55, 2.0 ** -7
+    eng = eng_cls.xxz(L, 1.0, D, tau0=tau0, dstar=64, sweeps=2, order=4)
+    eng.init()
+    sites, lnc, beta = eng.get_state()
+    rho, lnc_o = ox.init_rho(oh.xxz_chain_mpo(L, 1.0, D), tau0, 4, 64, 2, 1e-15)
+    assert beta == tau0
+    assert [w.shape[3] for w in sites] == [w.shape[3] for w in rho]
+    A = np.exp(lnc) * oh.mpo_to_dense(sites)
+    B = np.exp(lnc_o) * oh.mpo_to_dense(rho)
+    assert np.abs(A - B).max() <= 1e-13 * np.abs(B).max()
+
+
+def test_one_doubling_from_a_given_state(eng_cls):
+    """Feed the oracle's rho_n to the GPU and double once on both sides."""
+    from oracle import hamiltonian as oh
+    from oracle import xtrg as ox
+    L, D, tau0 = 7, 1.0, 2.0 ** -5
+    H = oh.xxz_chain_mpo(L, 1.0, D)
+    rows, states = ox.run_xtrg(H, tau0, 4, 20, 2, 3, 1e-15, keep_states=True)
+    rho, lnc = states[-1]
+    beta = rows[-1]["beta"]
+    eng = eng_cls.xxz(L, 1.0, D, tau0=tau0, dstar=20, sweeps=2, order=4)
+    eng.set_state(rho, lnc, beta)
+    eng.double()
+    g = eng.observables()
+    r2, lnc2 = ox.double(rho, lnc, 20, 2, 1e-15)
+    o = ox.observables(H, r2, lnc2, 2 * beta, L)
+    assert abs(g["lnZ"] - o["lnZ"]) <= 1e-11 * abs(o["lnZ"])
+    assert abs(g["u"] - o["u"]) <= 1e-11
+    sites, lncg, _ = eng.get_state()
+    A = np.exp(lncg) * oh.mpo_to_dense(sites)
+    B = np.exp(lnc2) * oh.mpo_to_dense(r2)
+    assert np.abs(A - B).max() <= 1e-11 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("L,dstar,order,sweeps", [(2, 4, 4, 1), (3, 1, 2, 1), (5, 3, 1, 3)])
+def test_edge_cases(eng_cls, L, dstar, order, sweeps):
+    """Shortest chain, D* = 1 (everything truncated to a product operator),
+    linear initialisation (Nc = 1), odd lengths."""
+    from oracle import hamiltonian as oh
+    from oracle import xtrg as ox
+    tau0, nd = 2.0 ** -6, 6
+    eng = eng_cls.xxz(L, 1.0, 0.9, tau0=tau0, dstar=dstar, sweeps=sweeps, order=order)
+    rows = eng.run(nd)
+    ref = ox.run_xtrg(oh.xxz_chain_mpo(L, 1.0, 0.9), tau0, order, dstar, sweeps, nd, 1e-15)
+    compare_rows(rows, ref, 1e-9, 1e-9, 1e-8)
+
+
+def test_errors_are_reported(eng_cls):
+    from paper_1801_00142_gb300 import _lib
+    eng = eng_cls.xxz(4, 1.0, 1.0, tau0=0.01, dstar=8, sweeps=1)
+    with pytest.raises(_lib.XtrgError) as e:
+        eng.double()          # before init
+    assert e.value.status == _lib.XTRG_EINVAL
+    assert "before xtrg_init" in _lib.xtrg_last_error(eng.ctx)
+    eng.init()
+    big = [np.ones((1, 2, 2, 40)), np.ones((40, 2, 2, 40)), np.ones((40, 2, 2, 1)), np.ones((1, 2, 2, 1))]
+    with pytest.raises(_lib.XtrgError):
+        eng.set_state(big, 0.0, 1.0)   # bond above the capacity D* + 1

@@ -135,6 +135,20 @@ xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* rho, double lnc, doubl
 xtrg_status xtrg_counters(const xtrg_ctx* ctx, double* contraction_flops, double* split_flops,
                           long long* two_site_updates);
 
+/* The tensor-core contraction primitive behind the XTRG_BF16X* modes, exposed
+ * on its own: C[b] = A[b] * B[b]^T for row-major FP64 device arrays
+ * A (batch x M x K), B (batch x N x K), C (batch x M x N).  A and B are split
+ * into `planes` BF16 planes (2 or 3); nprod products of planes are
+ * accumulated in FP32 on the tcgen05 tensor cores (1: x0*y0; 3: + x0*y1 +
+ * x1*y0; 6: + x0*y2 + x1*y1 + x2*y0); splitk > 1 splits K across CTAs and
+ * sums the partials in FP64.  workspace: device memory of at least
+ * xtrg_tc_gemm_workspace_bytes() bytes, 256-byte aligned.  Synchronises the
+ * stream.  Returns XTRG_ETIMEOUT if a bounded device wait expired. */
+size_t xtrg_tc_gemm_workspace_bytes(int M, int N, int K, int batch, int planes, int splitk);
+xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int N, int K,
+                         int batch, int planes, int nprod, int splitk, void* workspace,
+                         size_t workspace_bytes, void* cuda_stream);
+
 const char* xtrg_last_error(const xtrg_ctx* ctx);
 
 /* Free host bookkeeping.  The workspace stays the caller's. */

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "XTRG_OK", 1: "XTRG_EINVAL", 2: "XTRG_ENOMEM", 3: "XTRG_ECUDA
 # every exported symbol the header declares
 SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "xtrg_trace",
            "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_counters",
-           "xtrg_last_error", "xtrg_destroy"]
+           "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm"]
 
 
 class xtrg_mpo(C.Structure):
@@ -83,6 +83,10 @@ def _load():
     lib.xtrg_last_error.argtypes = [P]
     lib.xtrg_destroy.restype = None
     lib.xtrg_destroy.argtypes = [P]
+    lib.xtrg_tc_gemm_workspace_bytes.restype = C.c_size_t
+    lib.xtrg_tc_gemm_workspace_bytes.argtypes = [C.c_int] * 6
+    lib.xtrg_tc_gemm.restype = C.c_int
+    lib.xtrg_tc_gemm.argtypes = [P, P, P] + [C.c_int] * 7 + [P, C.c_size_t, P]
     return lib
 
 
@@ -169,6 +173,20 @@ def xtrg_counters(ctx):
     a, b, n = C.c_double(), C.c_double(), C.c_longlong()
     _check(ctx, LIB.xtrg_counters(ctx, C.byref(a), C.byref(b), C.byref(n)))
     return {"contraction_flops": a.value, "split_flops": b.value, "two_site_updates": n.value}
+
+
+def xtrg_tc_gemm_workspace_bytes(M, N, K, batch, planes, splitk) -> int:
+    return int(LIB.xtrg_tc_gemm_workspace_bytes(M, N, K, batch, planes, splitk))
+
+
+def xtrg_tc_gemm(A_ptr, B_ptr, C_ptr, M, N, K, batch, planes, nprod, splitk, ws_ptr, ws_bytes,
+                 stream):
+    """Device pointers in, status checked; C = A * B^T per batch (see xtrg.h)."""
+    s = LIB.xtrg_tc_gemm(C.c_void_p(A_ptr), C.c_void_p(B_ptr), C.c_void_p(C_ptr), M, N, K, batch,
+                         planes, nprod, splitk, C.c_void_p(ws_ptr), C.c_size_t(ws_bytes),
+                         C.c_void_p(stream))
+    if s != XTRG_OK:
+        raise XtrgError(s, "xtrg_tc_gemm")
 
 
 def xtrg_last_error(ctx) -> str:

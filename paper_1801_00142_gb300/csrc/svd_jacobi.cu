@@ -10,184 +10,220 @@
 // One-sided Jacobi orthogonalises the min(m, n) columns of M (or of M^T) by
 // plane rotations; it resolves small singular values to high relative
 // accuracy, which the series initialisation needs (its higher-order terms sit
-// 1e-10 .. 1e-15 below the leading singular value).  The rotations of one
-// round of the round-robin ordering act on disjoint column pairs and run as
-// one CTA per pair.
+// 1e-10 .. 1e-15 below the leading singular value).
+//
+// GPU mapping: one persistent cooperative kernel per split.  Each round of
+// the round-robin ordering rotates disjoint column pairs, one warp per pair
+// (shuffle reductions, no block barriers); rounds are separated by a grid
+// barrier whose wait is bounded (on expiry the kernel records a timeout and
+// every CTA leaves).  Convergence, the column norms, the selection of the
+// kept singular values and the emission of the two factors all happen inside
+// the same launch, so the host synchronises once per split to read k.
 #include <math.h>
 
 #include "common.cuh"
 
 namespace {
 
-constexpr int RT = 256;
+constexpr int WPB = 4;                  // warps per CTA
+constexpr int NT = WPB * 32;
+constexpr long long SPIN_LIMIT = 1LL << 22;
 
-__global__ void svd_load_kernel(const double* __restrict__ M, int m, int n, int trans,
-                                double* __restrict__ W, double* __restrict__ V, int len,
-                                int ncols) {
-  long long total = (long long)len * ncols;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    int j = (int)(e / len), i = (int)(e % len);
-    // column j of M (trans = 0, len = m) or of M^T (trans = 1, len = n)
-    W[e] = trans ? M[(long long)j * n + i] : M[(long long)i * n + j];
-  }
-  long long vt = (long long)ncols * ncols;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vt;
-       e += (long long)gridDim.x * blockDim.x) {
-    int j = (int)(e / ncols), i = (int)(e % ncols);
-    V[e] = (i == j) ? 1.0 : 0.0;
-  }
-}
+struct SvdArgs {
+  const double* M;
+  int m, n, trans, len, ncols, nn, kcap, mode, max_sweeps;
+  double tol, rel_tol;
+  double *W, *V, *sig;
+  int* perm;
+  double *left, *right;
+  unsigned* bar;      // [0] arrivals, [1] generation
+  int* rot;           // [3] rotations per sweep (ring)
+  int* out;           // [0] k, [1] rank, [2] sweeps, [3] status (0 ok, 1 timeout, 2 not converged)
+  double* stats;      // [0] total weight, [1] discarded fraction, [2] sigma_max
+};
 
-__device__ inline double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x / 32, l = threadIdx.x % 32;
+// Grid barrier with a bounded wait.  Returns false if the wait expired or
+// another CTA already recorded a timeout (then every CTA returns).
+__device__ bool grid_barrier(const SvdArgs& a) {
+  __shared__ int ok;
   __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x / 32); ++i) s += red[i];
-  return s;
-}
-
-__global__ void __launch_bounds__(RT) svd_round_kernel(double* __restrict__ W, double* __restrict__ V,
-                                                       int len, int ncols, int nn, int round,
-                                                       double tol, int* counter) {
-  __shared__ double red[3][RT / 32];
-  const int i = blockIdx.x;
-  const int mod = nn - 1;
-  int p, q;
-  if (i == 0) {
-    p = round;
-    q = nn - 1;
-  } else {
-    p = (round + i) % mod;
-    q = (round - i + mod) % mod;
-  }
-  if (p > q) { int t = p; p = q; q = t; }
-  if (q >= ncols) return;  // the padding column of an odd count
-  double* wp = W + (long long)p * len;
-  double* wq = W + (long long)q * len;
-  double a = 0.0, b = 0.0, g = 0.0;
-  for (int e = threadIdx.x; e < len; e += RT) {
-    double x = wp[e], y = wq[e];
-    a = fma(x, x, a);
-    b = fma(y, y, b);
-    g = fma(x, y, g);
-  }
-  a = block_sum(a, red[0]);
-  b = block_sum(b, red[1]);
-  g = block_sum(g, red[2]);
-  if (!(fabs(g) > tol * sqrt(a) * sqrt(b)) || a == 0.0 || b == 0.0) return;
-  // rotation zeroing the (p, q) Gram entry: tan = sign(z)/(|z| + sqrt(1+z^2))
-  double z = (b - a) / (2.0 * g);
-  double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + hypot(1.0, z));
-  double c = 1.0 / sqrt(1.0 + t * t);
-  double s = c * t;
-  for (int e = threadIdx.x; e < len; e += RT) {
-    double x = wp[e], y = wq[e];
-    wp[e] = c * x - s * y;
-    wq[e] = s * x + c * y;
-  }
-  double* vp = V + (long long)p * ncols;
-  double* vq = V + (long long)q * ncols;
-  for (int e = threadIdx.x; e < ncols; e += RT) {
-    double x = vp[e], y = vq[e];
-    vp[e] = c * x - s * y;
-    vq[e] = s * x + c * y;
-  }
-  if (threadIdx.x == 0) atomicAdd(counter, 1);
-}
-
-__global__ void svd_colnorm_kernel(const double* __restrict__ W, int len, double* __restrict__ sig) {
-  __shared__ double red[RT / 32];
-  const double* w = W + (long long)blockIdx.x * len;
-  double a = 0.0;
-  for (int e = threadIdx.x; e < len; e += RT) a = fma(w[e], w[e], a);
-  a = block_sum(a, red);
-  if (threadIdx.x == 0) sig[blockIdx.x] = sqrt(a);
-}
-
-// One CTA: rank the singular values (descending, ties by column index),
-// choose k = max(1, min(kcap, #{sigma > rel_tol * sigma_max})) and the
-// discarded weight.  Non-negative doubles order like their bit patterns.
-__global__ void svd_select_kernel(const double* __restrict__ sig, int ncols, int kcap,
-                                  double rel_tol, int* __restrict__ perm, int* __restrict__ kept,
-                                  double* __restrict__ stats) {
-  __shared__ double smax, stot;
-  __shared__ int scount;
-  if (threadIdx.x == 0) { smax = 0.0; stot = 0.0; scount = 0; }
-  __syncthreads();
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
-    long long bj = __double_as_longlong(sig[j]);
-    int r = 0;
-    for (int i = 0; i < ncols; ++i) {
-      long long bi = __double_as_longlong(sig[i]);
-      r += (bi > bj) || (bi == bj && i < j);
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vb = a.bar;
+    volatile int* st = a.out + 3;
+    if (*st == 1) {
+      ok = 0;
+    } else {
+      unsigned gen = vb[1];
+      __threadfence();
+      unsigned arrived = atomicAdd(a.bar, 1u);
+      if (arrived == gridDim.x - 1) {
+        vb[0] = 0;
+        __threadfence();
+        atomicAdd(a.bar + 1, 1u);
+      } else {
+        long long it = 0;
+        while (vb[1] == gen) {
+          if (++it > SPIN_LIMIT || *st == 1) {
+            atomicExch(a.out + 3, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
     }
-    perm[r] = j;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double mx = 0.0, tot = 0.0;
-    for (int j = 0; j < ncols; ++j) { mx = fmax(mx, sig[j]); tot += sig[j] * sig[j]; }
-    smax = mx;
-    stot = tot;
+  return ok != 0;
+}
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * WPB + (threadIdx.x >> 5);
+  const int TW = gridDim.x * WPB;
+  const long long gt = blockIdx.x * (long long)NT + threadIdx.x;
+  const long long GT = (long long)gridDim.x * NT;
+
+  // load: column j of M (trans = 0) or of M^T (trans = 1); V = I
+  const long long tot = (long long)a.len * a.ncols;
+  for (long long e = gt; e < tot; e += GT) {
+    int j = (int)(e / a.len), i = (int)(e % a.len);
+    a.W[e] = a.trans ? a.M[(long long)j * a.n + i] : a.M[(long long)i * a.n + j];
   }
-  __syncthreads();
-  int cnt = 0;
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) cnt += sig[j] > rel_tol * smax;
-  atomicAdd(&scount, cnt);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int k = scount;
-    if (k > kcap) k = kcap;
+  for (long long e = gt; e < (long long)a.ncols * a.ncols; e += GT) {
+    int j = (int)(e / a.ncols), i = (int)(e % a.ncols);
+    a.V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  if (gt < 3) a.rot[gt] = 0;
+  if (!grid_barrier(a)) return;
+
+  const int mod = a.nn - 1;
+  const int npairs = a.nn / 2;
+  int sweeps = 0;
+  bool converged = a.ncols < 2;
+  for (int s = 0; s < a.max_sweeps && !converged; ++s) {
+    if (gt == 0) a.rot[(s + 1) % 3] = 0;
+    int myrot = 0;
+    for (int r = 0; r < mod; ++r) {
+      for (int i = gw; i < npairs; i += TW) {
+        int p, q;
+        if (i == 0) { p = r; q = a.nn - 1; }
+        else { p = (r + i) % mod; q = (r - i + mod) % mod; }
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= a.ncols) continue;
+        double* wp = a.W + (long long)p * a.len;
+        double* wq = a.W + (long long)q * a.len;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int e = lane; e < a.len; e += 32) {
+          double x = wp[e], y = wq[e];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (!(fabs(ga) > a.tol * sqrt(al) * sqrt(be)) || al == 0.0 || be == 0.0) continue;
+        // rotation zeroing the (p, q) Gram entry: t = sign(z)/(|z| + sqrt(1+z^2))
+        double z = (be - al) / (2.0 * ga);
+        double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + hypot(1.0, z));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double sn = c * t;
+        for (int e = lane; e < a.len; e += 32) {
+          double x = wp[e], y = wq[e];
+          wp[e] = c * x - sn * y;
+          wq[e] = sn * x + c * y;
+        }
+        double* vp = a.V + (long long)p * a.ncols;
+        double* vq = a.V + (long long)q * a.ncols;
+        for (int e = lane; e < a.ncols; e += 32) {
+          double x = vp[e], y = vq[e];
+          vp[e] = c * x - sn * y;
+          vq[e] = sn * x + c * y;
+        }
+        ++myrot;
+      }
+      if (!grid_barrier(a)) return;
+    }
+    if (lane == 0 && myrot) atomicAdd(a.rot + (s % 3), myrot);
+    if (!grid_barrier(a)) return;
+    sweeps = s + 1;
+    converged = ((volatile int*)a.rot)[s % 3] == 0;
+  }
+
+  // column norms = singular values
+  for (int j = gw; j < a.ncols; j += TW) {
+    const double* w = a.W + (long long)j * a.len;
+    double s2 = 0.0;
+    for (int e = lane; e < a.len; e += 32) s2 = fma(w[e], w[e], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) a.sig[j] = sqrt(s2);
+  }
+  if (!grid_barrier(a)) return;
+
+  // rank the singular values (descending; ties by column index; non-negative
+  // doubles order like their bit patterns) and select k
+  for (int j = (int)gt; j < a.ncols; j += (int)GT) {
+    long long bj = __double_as_longlong(a.sig[j]);
+    int rk = 0;
+    for (int i = 0; i < a.ncols; ++i) {
+      long long bi = __double_as_longlong(a.sig[i]);
+      rk += (bi > bj) || (bi == bj && i < j);
+    }
+    a.perm[rk] = j;
+  }
+  if (!grid_barrier(a)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double mx = 0.0, totw = 0.0;
+    for (int j = 0; j < a.ncols; ++j) { mx = fmax(mx, a.sig[j]); totw += a.sig[j] * a.sig[j]; }
+    int cnt = 0;
+    for (int j = 0; j < a.ncols; ++j) cnt += a.sig[j] > a.rel_tol * mx;
+    int k = cnt < a.kcap ? cnt : a.kcap;
     if (k < 1) k = 1;
     double keptw = 0.0;
-    for (int r = 0; r < k; ++r) { double s = sig[perm[r]]; keptw += s * s; }
-    *kept = k;
-    stats[0] = stot;
-    stats[1] = stot > 0.0 ? fmax(0.0, (stot - keptw) / stot) : 0.0;
-    stats[2] = smax;
-    stats[3] = (double)scount;
+    for (int r = 0; r < k; ++r) { double s = a.sig[a.perm[r]]; keptw += s * s; }
+    a.out[0] = k;
+    a.out[1] = cnt;
+    a.out[2] = sweeps;
+    if (!converged) a.out[3] = 2;
+    a.stats[0] = totw;
+    a.stats[1] = totw > 0.0 ? fmax(0.0, (totw - keptw) / totw) : 0.0;
+    a.stats[2] = mx;
   }
-}
+  if (!grid_barrier(a)) return;
 
-// Left (m x k) and Right (k x n) factors from the converged rotation.
-// trans = 0: W = M V = U Sigma (len = m), V holds V.
-// trans = 1: W = M^T V' = V Sigma (len = n), V' holds U.
-__global__ void svd_emit_kernel(const double* __restrict__ W, const double* __restrict__ V,
-                                const double* __restrict__ sig, const int* __restrict__ perm,
-                                int k, int len, int ncols, int m, int n, int trans, int mode,
-                                double* __restrict__ left, double* __restrict__ right) {
-  long long nl = (long long)m * k, nr = (long long)k * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nl + nr;
-       e += (long long)gridDim.x * blockDim.x) {
+  // emit Left (m x k) and Right (k x n).
+  // trans = 0: W = M V = U Sigma (len = m), V holds V.
+  // trans = 1: W = M^T V' = V Sigma (len = n), V' holds U.
+  const int k = ((volatile int*)a.out)[0];
+  const long long nl = (long long)a.m * k, nr = (long long)k * a.n;
+  for (long long e = gt; e < nl + nr; e += GT) {
     bool isleft = e < nl;
     int r, x;
     if (isleft) { x = (int)(e / k); r = (int)(e % k); }
-    else { r = (int)((e - nl) / n); x = (int)((e - nl) % n); }
-    int j = perm[r];
-    double s = sig[j];
-    // is the stored column the Sigma-scaled vector (W) or a unit vector (V)?
-    bool fromW = isleft ? (trans == 0) : (trans == 1);
-    double base = fromW ? W[(long long)j * len + x] : V[(long long)j * ncols + x];
-    bool want_sigma = isleft ? (mode == SPLIT_LEFT) : (mode == SPLIT_RIGHT);
+    else { r = (int)((e - nl) / a.n); x = (int)((e - nl) % a.n); }
+    int j = a.perm[r];
+    double s = a.sig[j];
+    bool fromW = isleft ? (a.trans == 0) : (a.trans == 1);   // W holds Sigma-scaled vectors
+    double base = fromW ? a.W[(long long)j * a.len + x] : a.V[(long long)j * a.ncols + x];
+    bool want_sigma = isleft ? (a.mode == SPLIT_LEFT) : (a.mode == SPLIT_RIGHT);
     double v;
     if (want_sigma == fromW) v = base;
     else if (want_sigma) v = base * s;
     else v = (s > 0.0) ? base / s : 0.0;
-    if (isleft) left[(long long)x * k + r] = v;
-    else right[(long long)r * n + x] = v;
+    if (isleft) a.left[(long long)x * k + r] = v;
+    else a.right[(long long)r * a.n + x] = v;
   }
 }
 
-inline int grid_for(long long n) {
-  long long b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
-  if (b < 1) b = 1;
-  return (int)b;
-}
+int g_max_ctas = 0;
 
 }  // namespace
 
@@ -202,48 +238,55 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
       ncols > buf.max_cols)
     return cudaErrorInvalidValue;
   cudaError_t e;
-  svd_load_kernel<<<grid_for((long long)len * ncols), 256, 0, st>>>(M, m, n, trans, buf.W, buf.V,
-                                                                   len, ncols);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int nn = ncols + (ncols & 1);
-  const double tol = sqrt((double)len) * 2.220446049250313e-16;
-  const int max_sweeps = 60;
-  int sweeps = 0;
-  if (ncols > 1) {
-    for (; sweeps < max_sweeps; ++sweeps) {
-      if ((e = cudaMemsetAsync(buf.counter, 0, sizeof(int), st)) != cudaSuccess) return e;
-      for (int r = 0; r < nn - 1; ++r) {
-        svd_round_kernel<<<nn / 2, RT, 0, st>>>(buf.W, buf.V, len, ncols, nn, r, tol, buf.counter);
-      }
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      int h = 0;
-      if ((e = cudaMemcpyAsync(&h, buf.counter, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
-          cudaSuccess)
-        return e;
-      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-      if (h == 0) { ++sweeps; break; }
-    }
-    if (sweeps >= max_sweeps) *converged = false;
+  if (g_max_ctas == 0) {
+    int dev = 0, sms = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, svd_persistent, NT, 0)) !=
+        cudaSuccess)
+      return e;
+    g_max_ctas = sms * (per < 2 ? per : 2);
+    if (g_max_ctas < 1) return cudaErrorLaunchOutOfResources;
   }
-  svd_colnorm_kernel<<<ncols, RT, 0, st>>>(buf.W, len, buf.sig);
-  svd_select_kernel<<<1, 1024, 0, st>>>(buf.sig, ncols, kcap, rel_tol, buf.perm, buf.kept,
-                                        buf.stats);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int k = 0;
-  double stats[4];
-  if ((e = cudaMemcpyAsync(&k, buf.kept, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+  SvdArgs a;
+  a.M = M; a.m = m; a.n = n; a.trans = trans; a.len = len; a.ncols = ncols;
+  a.nn = ncols + (ncols & 1);
+  a.kcap = kcap; a.mode = (int)mode; a.max_sweeps = 60;
+  a.tol = sqrt((double)len) * 2.220446049250313e-16;
+  a.rel_tol = rel_tol;
+  a.W = buf.W; a.V = buf.V; a.sig = buf.sig; a.perm = buf.perm;
+  a.left = left; a.right = right;
+  a.bar = (unsigned*)buf.counter;      // 2 words
+  a.rot = buf.counter + 2;             // 3 words
+  a.out = buf.kept;                    // 4 words
+  a.stats = buf.stats;
+  if ((e = cudaMemsetAsync(buf.counter, 0, 8 * sizeof(int), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(buf.kept, 0, 4 * sizeof(int), st)) != cudaSuccess) return e;
+  int pairs = a.nn / 2;
+  int grid = (pairs + WPB - 1) / WPB;
+  long long work = (long long)len * ncols / (NT * 8);
+  if (work > grid) grid = (int)work;
+  if (grid > g_max_ctas) grid = g_max_ctas;
+  if (grid < 1) grid = 1;
+  void* args[] = {&a};
+  if ((e = cudaLaunchCooperativeKernel((void*)svd_persistent, dim3(grid), dim3(NT), args, 0, st)) !=
+      cudaSuccess)
     return e;
-  if ((e = cudaMemcpyAsync(stats, buf.stats, 4 * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+  int out[4];
+  double stats[3];
+  if ((e = cudaMemcpyAsync(out, buf.kept, sizeof out, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(stats, buf.stats, sizeof stats, cudaMemcpyDeviceToHost, st)) !=
       cudaSuccess)
     return e;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-  svd_emit_kernel<<<grid_for((long long)(m + n) * k), 256, 0, st>>>(
-      buf.W, buf.V, buf.sig, buf.perm, k, len, ncols, m, n, trans, (int)mode, left, right);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  res->k = k;
-  res->sweeps = sweeps;
+  if (out[3] == 1) return cudaErrorLaunchTimeout;
+  if (out[3] == 2) *converged = false;
+  res->k = out[0];
+  res->rank = out[1];
+  res->sweeps = out[2];
   res->discarded = stats[1];
   res->sigma_max = stats[2];
-  res->rank = (int)stats[3];
   return cudaSuccess;
 }

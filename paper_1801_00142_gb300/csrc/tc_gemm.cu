@@ -1,0 +1,370 @@
+// tcgen05 / TMA GEMM kernel (see tc_gemm.cuh).
+//
+// CTA tile 128 x 128 (M x N), K-block 64 BF16 = one 128-byte swizzle row.
+// Warp 0: TMA producer (one elected thread); warp 1: MMA issuer (one elected
+// thread, 4 x UMMA_K=16 per K-block and product); warp 2: tensor-memory
+// allocation; warps 4-7: epilogue (tcgen05.ld 32x32b, lane quarter = warp % 4).
+// Every mbarrier wait is bounded: on expiry the CTA records an error in
+// dev_err, drains its own outstanding TMA loads and MMAs (bounded again),
+// frees its tensor memory and returns.
+#include <stdint.h>
+
+#include "tc_gemm.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int TILE_BYTES = BM * BK * 2;       // 16 KB per operand plane and stage
+constexpr int NTHREADS = 256;
+constexpr long long WAIT_LIMIT = 1LL << 24;
+
+struct KParams {
+  int M, N, K, batch, splitk, kb_total, kb_per;
+  int pa_planes, pb_planes, nprod;
+  int prod_a[6], prod_b[6];
+  int a_batched, b_batched;
+  int stages;
+  TcOutput out;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait on an mbarrier phase; false (and *err set) on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 256) __nanosleep(64);
+    if ((i & 1023) == 1023 && *(volatile int*)err) return false;
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// K-major operand tile, 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for K-major SW128)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                 // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                 // swizzle mode: 128 B
+  return d;
+}
+
+// instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128
+__host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void store_out(const TcOutput& o, long long off, float v) {
+  if (o.mode == TC_OUT_BF16P) {
+    __nv_bfloat16 p0 = __float2bfloat16_rn(v);
+    float r = v - __bfloat162float(p0);
+    __nv_bfloat16 p1 = __float2bfloat16_rn(r);
+    o.bf16[off] = p0;
+    o.bf16[off + o.plane_stride] = p1;
+    if (o.planes > 2) {
+      float r2 = r - __bfloat162float(p1);
+      o.bf16[off + 2 * o.plane_stride] = __float2bfloat16_rn(r2);
+    }
+  } else {
+    o.f32[off] = v;
+  }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const KParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = p.stages;
+  const int stage_bytes = (p.pa_planes + p.pb_planes) * TILE_BYTES;
+  uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* done = empty + S;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int z = blockIdx.z;
+  const int bidx = z / p.splitk, split = z % p.splitk;
+  const int kb_begin = split * p.kb_per;
+  int kb_end = kb_begin + p.kb_per;
+  if (kb_end > p.kb_total) kb_end = p.kb_total;
+  const int nk = kb_end > kb_begin ? kb_end - kb_begin : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    const int ba = p.a_batched ? bidx : 0, bb = p.b_batched ? bidx : 0;
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % S;
+      if (i >= S) ok = mbar_wait(&empty[s], ((i / S) - 1) & 1, p.err);
+      if (!ok) break;
+      uint8_t* st = smem + s * stage_bytes;
+      mbar_expect_tx(&full[s], stage_bytes);
+      const int k0 = (kb_begin + i) * BK;
+      for (int q = 0; q < p.pa_planes; ++q)
+        tma_load_4d(st + q * TILE_BYTES, &mapA, &full[s], k0, m0, ba, q);
+      for (int q = 0; q < p.pb_planes; ++q)
+        tma_load_4d(st + (p.pa_planes + q) * TILE_BYTES, &mapB, &full[s], k0, n0, bb, q);
+      ++issued;
+    }
+    // drain: every load issued must have landed before the CTA may exit
+    for (int i = (issued > S ? issued - S : 0); i < issued; ++i)
+      mbar_wait(&full[i % S], (i / S) & 1, p.err);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_bf16_128x128();
+    bool ok = true;
+    int consumed = 0;
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % S;
+      ok = mbar_wait(&full[s], (i / S) & 1, p.err);
+      if (!ok) break;
+      fence_after();
+      const uint32_t base = smem_u32(smem + s * stage_bytes);
+      for (int pr = 0; pr < p.nprod; ++pr) {
+        const uint32_t a_addr = base + p.prod_a[pr] * TILE_BYTES;
+        const uint32_t b_addr = base + (p.pa_planes + p.prod_b[pr]) * TILE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          // advance 16 BF16 = 32 B along K inside the swizzled 128-B row
+          uint64_t da = smem_desc(a_addr) + (uint64_t)(kk * 2);
+          uint64_t db = smem_desc(b_addr) + (uint64_t)(kk * 2);
+          mma_bf16(tmem, da, db, idesc, (i > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&empty[s]);
+      ++consumed;
+    }
+    // the done barrier tracks completion of every MMA issued so far
+    mma_commit(done);
+  } else if (warp >= 4) {
+    // ---------------- epilogue
+    const int q = warp % 4;
+    const bool ok = mbar_wait(done, 0, p.err);
+    fence_after();
+    const int m = m0 + q * 32 + lane;
+    const TcOutput& o = p.out;
+    if (ok) {
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        if (nk > 0) {
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        }
+        if (m >= p.M) continue;
+        if (o.mode == TC_OUT_PARTIAL) {
+          float* dst = o.f32 + (((long long)split * p.batch + bidx) * p.M + m) * (long long)p.N;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (n0 + c + j < p.N) dst[n0 + c + j] = v[j];
+        } else {
+          const long long om = bidx * o.scb + idx_off(o.cm, m);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c + j;
+            if (n < p.N) store_out(o, om + idx_off(o.cn, n), (float)o.alpha * v[j]);
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                             CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                             CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+  }
+  return fn;
+}
+
+// 4-D map: (k, rows, batch, plane), box (64, 128, 1, 1), 128-byte swizzle,
+// out-of-range elements read as zero.
+cudaError_t make_map(CUtensorMap* map, const TcOperand& op) {
+  EncodeFn enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  if (op.ld % 8 != 0 || op.ld < op.k || ((uintptr_t)op.base % 16) != 0) return cudaErrorInvalidValue;
+  const long long bstride = op.batches > 1 ? op.batch_stride : (long long)op.rows * op.ld;
+  cuuint64_t dims[4] = {(cuuint64_t)op.k, (cuuint64_t)op.rows, (cuuint64_t)op.batches,
+                        (cuuint64_t)op.planes};
+  cuuint64_t strides[3] = {(cuuint64_t)op.ld * 2, (cuuint64_t)bstride * 2,
+                           (cuuint64_t)op.plane_stride * 2};
+  if ((strides[1] % 16) || (strides[2] % 16)) return cudaErrorInvalidValue;
+  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)BM, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)op.base, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K, int batch,
+                    int nprod, int splitk, const TcOutput& out, int* dev_err, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (K <= 0 || splitk < 1 || batch * splitk > 65535) return cudaErrorInvalidValue;
+  if (A.rows < M || B.rows < N || A.k != K || B.k != K) return cudaErrorInvalidValue;
+  if ((A.batches != 1 && A.batches != batch) || (B.batches != 1 && B.batches != batch))
+    return cudaErrorInvalidValue;
+  if (splitk > 1 && out.mode != TC_OUT_PARTIAL) return cudaErrorInvalidValue;
+  KParams p;
+  p.M = M; p.N = N; p.K = K; p.batch = batch; p.splitk = splitk;
+  p.kb_total = (K + BK - 1) / BK;
+  p.kb_per = (p.kb_total + splitk - 1) / splitk;
+  p.pa_planes = A.planes;
+  p.pb_planes = B.planes;
+  static const int pa6[6] = {0, 0, 1, 0, 1, 2}, pb6[6] = {0, 1, 0, 2, 1, 0};
+  if (nprod != 1 && nprod != 3 && nprod != 6) return cudaErrorInvalidValue;
+  for (int i = 0; i < nprod; ++i) {
+    p.prod_a[i] = pa6[i];
+    p.prod_b[i] = pb6[i];
+    if (pa6[i] >= A.planes || pb6[i] >= B.planes) return cudaErrorInvalidValue;
+  }
+  p.nprod = nprod;
+  p.a_batched = A.batches > 1;
+  p.b_batched = B.batches > 1;
+  const int stage_bytes = (A.planes + B.planes) * TILE_BYTES;
+  int S = (200 * 1024) / stage_bytes;
+  if (S > 4) S = 4;
+  if (S < 2) return cudaErrorInvalidValue;
+  p.stages = S;
+  p.out = out;
+  p.err = dev_err;
+  CUtensorMap ma, mb;
+  cudaError_t e;
+  if ((e = make_map(&ma, A)) != cudaSuccess) return e;
+  if ((e = make_map(&mb, B)) != cudaSuccess) return e;
+  const int smem = S * stage_bytes + 1024 + (2 * S + 2) * 8 + 64;
+  static bool attr_done = false;
+  if (!attr_done) {
+    if ((e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024)) != cudaSuccess)
+      return e;
+    attr_done = true;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splitk);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  tc_gemm_kernel<<<grid, NTHREADS, smem, st>>>(ma, mb, p);
+  return cudaGetLastError();
+}

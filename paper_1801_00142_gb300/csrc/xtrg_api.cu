@@ -31,6 +31,8 @@
 #include "../../include/xtrg.h"
 #include "common.cuh"
 #include "mixed.cuh"
+#include "mixed_ops.cuh"
+#include "tc_gemm.cuh"
 
 namespace {
 
@@ -41,8 +43,9 @@ struct DevMpo {
 };
 
 struct Plan {
-  int L, DH, cap, cap_fat, fat_bond;
-  size_t n_h, n_site, n_fat, n_pp, n_env, n_part, n_ce, n_svd, n_svd_cols, n_usbuf, n_obs;
+  int L, DH, cap, cap_fat, fat_bond, capc;
+  size_t n_h, n_site, n_csite, n_fat, n_pp, n_env, n_part, n_ce, n_svd, n_svd_cols, n_usbuf,
+      n_obs;
   size_t mixed_bytes;
   size_t total;
 };
@@ -50,6 +53,11 @@ struct Plan {
 constexpr size_t ALIGN = 256;
 inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
+// Capacities: rho and the Horner iterate Y have bonds <= cap = D* + 1.  The
+// compressed MPO C starts from a right-canonicalised guess whose bonds can
+// exceed D* before the sweeps truncate them: for the exact-product guess of
+// the series products they are bounded by the fused bond DH * cap_fat, so C
+// and everything shaped by C's bonds use capc = max(cap, DH * cap_fat).
 bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
   if (L < 2 || DH < 1 || cfg->dstar < 1 || cfg->dstar > 1024) return false;
   p->L = L;
@@ -57,28 +65,28 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
   p->cap = cfg->dstar + 1;
   p->cap_fat = p->cap < 64 ? p->cap : 64;
   p->fat_bond = DH * p->cap_fat;
-  const size_t cap = p->cap;
-  const size_t fb = p->fat_bond;
-  const size_t big = fb > cap ? fb : cap;
+  p->capc = p->cap > p->fat_bond ? p->cap : p->fat_bond;
+  const size_t cap = p->cap, capc = p->capc, fb = p->fat_bond;
+  const size_t da = cap > (size_t)DH ? cap : (size_t)DH;    // bound of A's bonds
   p->n_h = (size_t)DH * 4 * DH;
   p->n_site = cap * 4 * cap;
+  p->n_csite = capc * 4 * capc;
   p->n_fat = fb * 4 * fb;
-  p->n_pp = big * 4 * cap;
-  size_t dab = (cap > (size_t)DH ? cap : (size_t)DH) * cap;   // Da*Db bound
-  p->n_env = dab * cap;
-  p->n_part = 4 * cap * dab;
-  p->n_ce = 16 * cap * cap;
-  size_t s1 = 16 * cap * cap, s2 = 4 * cap * big;
-  p->n_svd = s1 > s2 ? s1 : s2;
-  p->n_svd_cols = (4 * cap > big ? 4 * cap : big);
-  p->n_usbuf = big * cap;
+  p->n_pp = capc * 4 * capc;
+  p->n_env = da * cap * capc;
+  p->n_part = 4 * capc * da * cap;
+  p->n_ce = 16 * capc * capc;
+  p->n_svd = 16 * capc * capc;
+  p->n_svd_cols = 4 * capc;
+  p->n_usbuf = capc * capc;
   p->n_obs = (size_t)DH * DH * 4 * cap * 2;
   p->mixed_bytes = (cfg->prec == XTRG_FP64) ? 0 : mixed_workspace_bytes(L, p->cap, DH);
   size_t t = 0;
   t += up((size_t)L * p->n_h * 8);          // H
   t += up((size_t)L * 4 * 8);               // identity sites
-  t += 3 * up((size_t)L * p->n_site * 8);   // rho, C, Y
-  t += up((size_t)L * p->n_fat * 8);        // fat guess
+  t += up((size_t)L * p->n_site * 8);       // Y
+  t += 2 * up((size_t)L * p->n_csite * 8);  // rho, C (swapped after every product)
+  t += up((size_t)L * p->n_fat * 8);        // exact-product guess
   t += 2 * up(p->n_pp * 8);                 // canonicalisation ping-pong
   t += up((size_t)(L + 1) * p->n_env * 8);  // environments
   t += 3 * up(p->n_part * 8);               // T1, Lpart, Rpart
@@ -200,6 +208,8 @@ xtrg_status split(xtrg_ctx* ctx, const double* M, int m, int n, int kcap, SplitM
   bool conv = true;
   cudaError_t e = svd_split_f64(M, m, n, kcap, ctx->cfg.svd_rel_tol, mode, left, right, ctx->svd,
                                 ctx->st, r, &conv);
+  if (e == cudaErrorLaunchTimeout)
+    return fail(ctx, XTRG_ETIMEOUT, "svd split %dx%d: a bounded device barrier expired", m, n);
   if (e != cudaSuccess) return fail(ctx, XTRG_ECUDA, "svd split %dx%d: %s", m, n, cudaGetErrorString(e));
   if (!conv) return fail(ctx, XTRG_ENUMERIC, "Jacobi SVD of a %dx%d matrix did not converge", m, n);
   if (!std::isfinite(r->sigma_max)) return fail(ctx, XTRG_ENUMERIC, "non-finite singular value");
@@ -219,9 +229,10 @@ xtrg_status canonicalize(xtrg_ctx* ctx, const std::vector<int>& sdims,
   C.dims[L] = 1;
   for (int i = L - 1; i >= 1; --i) {
     SvdResult r;
-    TRY(split(ctx, cur, cl, 4 * cr, ctx->cap, SPLIT_LEFT, ctx->usbuf, C.site[i], &r));
-    if (r.rank > ctx->cap)
-      return fail(ctx, XTRG_ENOMEM, "canonical bond at site %d exceeds capacity %d", i, ctx->cap);
+    TRY(split(ctx, cur, cl, 4 * cr, ctx->plan.capc, SPLIT_LEFT, ctx->usbuf, C.site[i], &r));
+    if (r.rank > ctx->plan.capc)
+      return fail(ctx, XTRG_ENOMEM, "canonical bond at site %d exceeds capacity %d", i,
+                  ctx->plan.capc);
     C.dims[i] = r.k;
     // site i-1 times (U Lambda): (l' * 4) x cl times cl x k
     int lp = sdims[i - 1];
@@ -455,7 +466,7 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   ctx->DH = p.DH;
   ctx->cap = p.cap;
   bool ok = carve_mpo(ctx, &ctx->H, p.n_h) && carve_mpo(ctx, &ctx->I, 4) &&
-            carve_mpo(ctx, &ctx->rho, p.n_site) && carve_mpo(ctx, &ctx->C, p.n_site) &&
+            carve_mpo(ctx, &ctx->rho, p.n_csite) && carve_mpo(ctx, &ctx->C, p.n_csite) &&
             carve_mpo(ctx, &ctx->Y, p.n_site) && carve_mpo(ctx, &ctx->fat, p.n_fat);
   ctx->pp[0] = (double*)carve(ctx, p.n_pp * 8);
   ctx->pp[1] = (double*)carve(ctx, p.n_pp * 8);
@@ -648,6 +659,69 @@ extern "C" xtrg_status xtrg_counters(const xtrg_ctx* ctx, double* cf, double* sf
   if (sf) *sf = ctx->flops_split;
   if (upd) *upd = ctx->updates;
   return XTRG_OK;
+}
+
+namespace {
+struct TcWs {
+  size_t a, b, part, total;
+};
+TcWs tc_ws(int M, int N, int K, int batch, int planes, int splitk) {
+  TcWs w;
+  const size_t ld = (size_t)tc_ld(K);
+  w.a = up((size_t)planes * batch * M * ld * 2);
+  w.b = up((size_t)planes * batch * N * ld * 2);
+  w.part = up((size_t)splitk * batch * M * N * 4);
+  w.total = w.a + w.b + w.part + ALIGN;
+  return w;
+}
+}  // namespace
+
+extern "C" size_t xtrg_tc_gemm_workspace_bytes(int M, int N, int K, int batch, int planes,
+                                               int splitk) {
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || planes < 1 || planes > 3 || splitk < 1) return 0;
+  return tc_ws(M, N, K, batch, planes, splitk).total;
+}
+
+extern "C" xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int N,
+                                    int K, int batch, int planes, int nprod, int splitk,
+                                    void* workspace, size_t bytes, void* stream) {
+  if (!A || !B || !C || !workspace || ((uintptr_t)workspace % ALIGN) != 0) return XTRG_EINVAL;
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || planes < 2 || planes > 3 || splitk < 1)
+    return XTRG_EINVAL;
+  if (!(nprod == 1 || nprod == 3 || (nprod == 6 && planes == 3))) return XTRG_EINVAL;
+  const TcWs w = tc_ws(M, N, K, batch, planes, splitk);
+  if (bytes < w.total) return XTRG_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = (char*)workspace;
+  __nv_bfloat16* pa = (__nv_bfloat16*)base;
+  __nv_bfloat16* pb = (__nv_bfloat16*)(base + w.a);
+  float* part = (float*)(base + w.a + w.b);
+  int* err = (int*)(base + w.a + w.b + w.part);
+  const long long ld = tc_ld(K);
+  const long long psA = (long long)batch * M * ld, psB = (long long)batch * N * ld;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return XTRG_ECUDA;
+  if (to_planes(A, idx_plain(K), idx_plain(1), (long long)M * K, M, K, batch, pa, ld,
+                (long long)M * ld, planes, psA, st) != cudaSuccess)
+    return XTRG_ECUDA;
+  if (to_planes(B, idx_plain(K), idx_plain(1), (long long)N * K, N, K, batch, pb, ld,
+                (long long)N * ld, planes, psB, st) != cudaSuccess)
+    return XTRG_ECUDA;
+  TcOperand oa{pa, planes, M, K, ld, (long long)M * ld, psA, batch};
+  TcOperand ob{pb, planes, N, K, ld, (long long)N * ld, psB, batch};
+  TcOutput out;
+  memset(&out, 0, sizeof out);
+  out.mode = TC_OUT_PARTIAL;
+  out.f32 = part;
+  out.alpha = 1.0;
+  if (tc_gemm(oa, ob, M, N, K, batch, nprod, splitk, out, err, st) != cudaSuccess)
+    return XTRG_ECUDA;
+  if (reduce_partials(part, splitk, (long long)batch * M * N, C, st) != cudaSuccess)
+    return XTRG_ECUDA;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return XTRG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return XTRG_ECUDA;
+  return h ? XTRG_ETIMEOUT : XTRG_OK;
 }
 
 extern "C" const char* xtrg_last_error(const xtrg_ctx* ctx) {

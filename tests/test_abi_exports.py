@@ -55,6 +55,24 @@ def test_workspace_bytes_and_input_checks(lib):
     assert e.value.status == lib.XTRG_ENOMEM
 
 
+@pytest.mark.parametrize("L,dstar", [(2, 1), (4, 16), (8, 256), (64, 256), (10, 3)])
+def test_workspace_plan_covers_every_buffer(lib, L, dstar):
+    """With exactly xtrg_workspace_bytes() the carving of every buffer fits:
+    on a machine without a GPU, create then fails at its first device copy
+    (XTRG_ECUDA), never at carving (XTRG_ENOMEM)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    from paper_1801_00142_gb300.hamiltonians import xxz_chain
+    dims, sites = xxz_chain(L)
+    H = lib.MpoArgs(dims, sites)
+    cfg = lib.make_config(2 ** -10, 4, dstar, 2)
+    n = lib.xtrg_workspace_bytes(H, cfg)
+    with pytest.raises(lib.XtrgError) as e:
+        lib.xtrg_create(H, cfg, 1 << 20, n, 0)
+    assert e.value.status == lib.XTRG_ECUDA
+
+
 def test_hamiltonian_builder_is_the_xxz_chain(lib):
     import numpy as np
 

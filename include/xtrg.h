@@ -55,11 +55,12 @@ typedef enum {
 
 /* Arithmetic of the environment and two-site contractions (the O(D^4 d^3)
  * part).  Splitting, canonicalisation, normalisation and traces are FP64 in
- * every mode. */
+ * every mode.  The tensor-core modes store every contraction operand as BF16
+ * planes x ~= x0 + x1 (+ x2) and accumulate products of planes in FP32. */
 typedef enum {
-  XTRG_FP64 = 0,      /* FP64 CUDA-core contractions                          */
-  XTRG_TF32X3 = 1,    /* tcgen05 tensor cores, 3-term split TF32, FP32 accumulate */
-  XTRG_BF16X3 = 2     /* tcgen05 tensor cores, 3-term split BF16, FP32 accumulate */
+  XTRG_FP64 = 0,      /* FP64 CUDA-core contractions                           */
+  XTRG_BF16X6 = 1,    /* tcgen05, 3 planes, 6 products: ~24 significant bits   */
+  XTRG_BF16X3 = 2     /* tcgen05, 2 planes, 3 products: ~16 significant bits   */
 } xtrg_precision;
 
 /* An MPO given by host arrays (see conventions above). */
@@ -126,14 +127,31 @@ xtrg_status xtrg_observables(xtrg_ctx* ctx, xtrg_obs* out);
 xtrg_status xtrg_get_state(xtrg_ctx* ctx, int* bond_dims, double* const* W, double* lnc,
                            double* beta);
 
-/* Replace the current rho by a host MPO (any gauge), its log scale lnc and
- * its beta.  Bonds must not exceed the context's capacity (D* + 1). */
-xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* rho, double lnc, double beta);
+/* Replace the current rho by a host MPO, its log scale lnc and its beta.
+ * Bonds must not exceed the context's capacity (D* + 1).  right_canonical:
+ * nonzero if sites 1..L-1 are right-orthonormal (as every state returned by
+ * xtrg_get_state is), which lets the next doubling skip re-canonicalising;
+ * zero for an MPO in any gauge. */
+xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* rho, double lnc, double beta,
+                           int right_canonical);
 
-/* Work counters since creation: flops of the contraction GEMMs (algorithmic,
- * 2*M*N*K per GEMM) and of the FP64 splitting, and device time is not kept. */
-xtrg_status xtrg_counters(const xtrg_ctx* ctx, double* contraction_flops, double* split_flops,
-                          long long* two_site_updates);
+typedef struct {
+  double contraction_flops;  /* algorithmic 2*M*N*K of every contraction GEMM       */
+  double split_flops;        /* estimated flops of the truncation (split)           */
+  double tc_flops;           /* algorithmic flops of the tensor-core GEMM launches   */
+  double tc_ms;              /* their summed device time (only while profiling)      */
+  long long two_site_updates;
+  long long tc_launches;     /* tensor-core GEMM launches (only while profiling)     */
+  long long kernel_launches; /* kernels launched by this library, all contexts      */
+} xtrg_stats;
+
+/* Counters since creation (kernel_launches: since the library was loaded). */
+xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* out);
+
+/* on != 0: time every tensor-core GEMM launch with CUDA events on the
+ * context's stream (adds event records; results resolved at the end of each
+ * product, which synchronises anyway). */
+xtrg_status xtrg_set_profiling(xtrg_ctx* ctx, int on);
 
 /* The tensor-core contraction primitive behind the XTRG_BF16X* modes, exposed
  * on its own: C[b] = A[b] * B[b]^T for row-major FP64 device arrays

@@ -15,14 +15,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libxtrg.so")
 
 XTRG_OK, XTRG_EINVAL, XTRG_ENOMEM, XTRG_ECUDA, XTRG_ENUMERIC, XTRG_ETIMEOUT = range(6)
-XTRG_FP64, XTRG_TF32X3, XTRG_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp64": XTRG_FP64, "tf32x3": XTRG_TF32X3, "bf16x3": XTRG_BF16X3}
+XTRG_FP64, XTRG_BF16X6, XTRG_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": XTRG_FP64, "bf16x6": XTRG_BF16X6, "bf16x3": XTRG_BF16X3}
 STATUS_NAMES = {0: "XTRG_OK", 1: "XTRG_EINVAL", 2: "XTRG_ENOMEM", 3: "XTRG_ECUDA",
                 4: "XTRG_ENUMERIC", 5: "XTRG_ETIMEOUT"}
 
 # every exported symbol the header declares
 SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "xtrg_trace",
-           "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_counters",
+           "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_get_stats",
+           "xtrg_set_profiling",
            "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm"]
 
 
@@ -42,6 +43,16 @@ class xtrg_obs(C.Structure):
                 ("u", C.c_double), ("c", C.c_double), ("lnZ2", C.c_double),
                 ("trunc_err", C.c_double), ("herm_defect", C.c_double),
                 ("max_bond", C.c_int), ("n_doublings", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class xtrg_stats(C.Structure):
+    _fields_ = [("contraction_flops", C.c_double), ("split_flops", C.c_double),
+                ("tc_flops", C.c_double), ("tc_ms", C.c_double),
+                ("two_site_updates", C.c_longlong), ("tc_launches", C.c_longlong),
+                ("kernel_launches", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,10 +86,11 @@ def _load():
     lib.xtrg_get_state.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.POINTER(C.c_double)),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.xtrg_set_state.restype = C.c_int
-    lib.xtrg_set_state.argtypes = [P, C.POINTER(xtrg_mpo), C.c_double, C.c_double]
-    lib.xtrg_counters.restype = C.c_int
-    lib.xtrg_counters.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
-                                  C.POINTER(C.c_longlong)]
+    lib.xtrg_set_state.argtypes = [P, C.POINTER(xtrg_mpo), C.c_double, C.c_double, C.c_int]
+    lib.xtrg_get_stats.restype = C.c_int
+    lib.xtrg_get_stats.argtypes = [P, C.POINTER(xtrg_stats)]
+    lib.xtrg_set_profiling.restype = C.c_int
+    lib.xtrg_set_profiling.argtypes = [P, C.c_int]
     lib.xtrg_last_error.restype = C.c_char_p
     lib.xtrg_last_error.argtypes = [P]
     lib.xtrg_destroy.restype = None
@@ -163,16 +175,21 @@ def xtrg_get_state(ctx, L):
     return sites, lnc.value, beta.value
 
 
-def xtrg_set_state(ctx, sites, lnc, beta):
+def xtrg_set_state(ctx, sites, lnc, beta, right_canonical=False):
     dims = [1] + [w.shape[3] for w in sites]
     m = MpoArgs(dims, sites)
-    _check(ctx, LIB.xtrg_set_state(ctx, C.byref(m.struct), float(lnc), float(beta)))
+    _check(ctx, LIB.xtrg_set_state(ctx, C.byref(m.struct), float(lnc), float(beta),
+                                   1 if right_canonical else 0))
 
 
-def xtrg_counters(ctx):
-    a, b, n = C.c_double(), C.c_double(), C.c_longlong()
-    _check(ctx, LIB.xtrg_counters(ctx, C.byref(a), C.byref(b), C.byref(n)))
-    return {"contraction_flops": a.value, "split_flops": b.value, "two_site_updates": n.value}
+def xtrg_get_stats(ctx) -> dict:
+    o = xtrg_stats()
+    _check(ctx, LIB.xtrg_get_stats(ctx, C.byref(o)))
+    return o.as_dict()
+
+
+def xtrg_set_profiling(ctx, on):
+    _check(ctx, LIB.xtrg_set_profiling(ctx, 1 if on else 0))
 
 
 def xtrg_tc_gemm_workspace_bytes(M, N, K, batch, planes, splitk) -> int:

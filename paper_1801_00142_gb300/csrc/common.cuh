@@ -3,6 +3,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Number of kernels this library has launched (all contexts, all streams);
+// every launch site calls note_launch().
+extern unsigned long long g_xtrg_launches;
+static inline void note_launch() { __atomic_add_fetch(&g_xtrg_launches, 1ull, __ATOMIC_RELAXED); }
+
 // A strided view of one GEMM index.  The index idx in [0, n2*n1*n0) is split
 // as idx = (i2*n1 + i1)*n0 + i0 and lands at element offset
 // i2*s2 + i1*s1 + i0*s0.  A plain stride s is {1, 1, s, 0, 0}.
@@ -40,6 +45,16 @@ struct GemmF64 {
 };
 
 cudaError_t gemm_f64(const GemmF64& g, cudaStream_t st);
+
+// The same contract in FP32 (small contractions of the tensor-core path's truncation).
+struct GemmF32 {
+  int M, N, K, batch;
+  const float* A; Idx3 am, ak; long long sab;
+  const float* B; Idx3 bk, bn; long long sbb;
+  float* C; Idx3 cm, cn; long long scb;
+  double alpha, beta;
+};
+cudaError_t gemm_f32(const GemmF32& g, cudaStream_t st);
 
 // ---------------------------------------------------------------- SVD split
 // One-sided (Hestenes) Jacobi SVD of a row-major m x n matrix M in FP64,

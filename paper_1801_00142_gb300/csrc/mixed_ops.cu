@@ -16,7 +16,8 @@ inline int grid_for(long long n) {
 
 // out[b][r][k] (row stride ld, batch stride obs, plane stride ops) =
 // split(src[b*sbs + off(rv, r) + off(kv, k)]); padding columns k in [K, ld) = 0
-__global__ void to_planes_kernel(const double* __restrict__ src, Idx3 rv, Idx3 kv, long long sbs,
+template <typename S>
+__global__ void to_planes_kernel(const S* __restrict__ src, Idx3 rv, Idx3 kv, long long sbs,
                                  int rows, int K, int batch, __nv_bfloat16* __restrict__ out,
                                  long long ld, long long obs, int planes, long long ops) {
   const long long per = (long long)rows * ld;
@@ -27,7 +28,7 @@ __global__ void to_planes_kernel(const double* __restrict__ src, Idx3 rv, Idx3 k
     const long long w = e % per;
     const int r = (int)(w / ld), k = (int)(w % ld);
     double x = 0.0;
-    if (k < K) x = src[b * sbs + idx_off(rv, r) + idx_off(kv, k)];
+    if (k < K) x = (double)src[b * sbs + idx_off(rv, r) + idx_off(kv, k)];
     const __nv_bfloat16 p0 = __double2bfloat16(x);
     const double r1 = x - (double)__bfloat162float(p0);
     const __nv_bfloat16 p1 = __double2bfloat16(r1);
@@ -48,6 +49,28 @@ __global__ void relayout_planes_kernel(const __nv_bfloat16* __restrict__ src, Id
     const long long so = (k < K) ? idx_off(rv, r) + idx_off(kv, k) : -1;
     for (int p = 0; p < planes; ++p)
       out[e + p * ops] = so >= 0 ? src[so + p * sps] : __float2bfloat16_rn(0.f);
+  }
+}
+
+// out[p][r][k] = src[p][k][r] for r < rows, k < K (32 x 32 tiles through shared
+// memory, coalesced on both sides); padding columns K <= k < ld are zeroed.
+__global__ void transpose_planes_kernel(const __nv_bfloat16* __restrict__ src, long long sld,
+                                        int rows, int K, __nv_bfloat16* __restrict__ out,
+                                        long long ld, long long sps, long long ops) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int p = blockIdx.z;
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const __nv_bfloat16* sp = src + p * sps;
+  __nv_bfloat16* op = out + p * ops;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8 threads
+  for (int y = ty; y < 32; y += 8) {
+    const int k = k0 + y, r = r0 + tx;
+    tile[y][tx] = (k < K && r < rows) ? sp[(long long)k * sld + r] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  for (int y = ty; y < 32; y += 8) {
+    const int r = r0 + y, k = k0 + tx;
+    if (r < rows && k < ld) op[(long long)r * ld + k] = tile[tx][y];
   }
 }
 
@@ -74,8 +97,30 @@ cudaError_t to_planes(const double* src, Idx3 rv, Idx3 kv, long long sbs, int ro
                       long long ops, cudaStream_t st) {
   long long total = (long long)rows * ld * batch;
   if (total <= 0) return cudaSuccess;
-  to_planes_kernel<<<grid_for(total), 256, 0, st>>>(src, rv, kv, sbs, rows, K, batch, out, ld,
-                                                    obs, planes, ops);
+  note_launch();
+  to_planes_kernel<double><<<grid_for(total), 256, 0, st>>>(src, rv, kv, sbs, rows, K, batch, out,
+                                                            ld, obs, planes, ops);
+  return cudaGetLastError();
+}
+
+cudaError_t to_planes_f32(const float* src, Idx3 rv, Idx3 kv, long long sbs, int rows, int K,
+                          int batch, __nv_bfloat16* out, long long ld, long long obs, int planes,
+                          long long ops, cudaStream_t st) {
+  long long total = (long long)rows * ld * batch;
+  if (total <= 0) return cudaSuccess;
+  note_launch();
+  to_planes_kernel<float><<<grid_for(total), 256, 0, st>>>(src, rv, kv, sbs, rows, K, batch, out,
+                                                           ld, obs, planes, ops);
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_planes(const __nv_bfloat16* src, long long sld, int rows, int K,
+                             __nv_bfloat16* out, long long ld, int planes, long long sps,
+                             long long ops, cudaStream_t st) {
+  if (rows <= 0 || ld <= 0) return cudaSuccess;
+  dim3 grid((rows + 31) / 32, (int)((ld + 31) / 32), planes);
+  note_launch();
+  transpose_planes_kernel<<<grid, 256, 0, st>>>(src, sld, rows, K, out, ld, sps, ops);
   return cudaGetLastError();
 }
 
@@ -84,6 +129,7 @@ cudaError_t relayout_planes(const __nv_bfloat16* src, Idx3 rv, Idx3 kv, int rows
                             long long ops, cudaStream_t st) {
   long long total = (long long)rows * ld;
   if (total <= 0) return cudaSuccess;
+  note_launch();
   relayout_planes_kernel<<<grid_for(total), 256, 0, st>>>(src, rv, kv, rows, K, out, ld, planes,
                                                           sps, ops);
   return cudaGetLastError();
@@ -91,11 +137,13 @@ cudaError_t relayout_planes(const __nv_bfloat16* src, Idx3 rv, Idx3 kv, int rows
 
 cudaError_t reduce_partials(const float* part, int splits, long long n, double* out,
                             cudaStream_t st) {
+  note_launch();
   reduce_partials_kernel<<<grid_for(n), 256, 0, st>>>(part, splits, n, out);
   return cudaGetLastError();
 }
 
 cudaError_t f32_to_f64(const float* a, long long n, double* b, cudaStream_t st) {
+  note_launch();
   f32_to_f64_kernel<<<grid_for(n), 256, 0, st>>>(a, n, b);
   return cudaGetLastError();
 }

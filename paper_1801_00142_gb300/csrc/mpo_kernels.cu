@@ -3,6 +3,8 @@
 // Eq. RhoTau, and FP64 fill/scale/norm helpers used by the normalisation.
 #include "common.cuh"
 
+unsigned long long g_xtrg_launches = 0;
+
 namespace {
 
 inline int grid_for(long long n) {
@@ -108,6 +110,7 @@ __global__ void identity_site_kernel(double* p) {
 cudaError_t mpo_exact_product(const double* A, int la, int ra, const double* B, int lb, int rb,
                               double* G, cudaStream_t st) {
   long long total = (long long)la * lb * 4 * ra * rb;
+  note_launch();
   exact_product_kernel<<<grid_for(total), 256, 0, st>>>(A, la, ra, B, lb, rb, G);
   return cudaGetLastError();
 }
@@ -118,27 +121,32 @@ cudaError_t mpo_direct_sum_site(const double* P, int pl, int pr, double alpha, c
   int ol = first ? 1 : pl + ql;
   int orr = last ? 1 : pr + qr;
   long long total = (long long)ol * 4 * orr;
+  note_launch();
   direct_sum_kernel<<<grid_for(total), 256, 0, st>>>(P, pl, pr, alpha, Q, ql, qr, first, last, ol,
                                                      orr, out);
   return cudaGetLastError();
 }
 
 cudaError_t dev_fill(double* p, double v, long long n, cudaStream_t st) {
+  note_launch();
   fill_kernel<<<grid_for(n), 256, 0, st>>>(p, v, n);
   return cudaGetLastError();
 }
 
 cudaError_t dev_scale(double* p, double v, long long n, cudaStream_t st) {
+  note_launch();
   scale_kernel<<<grid_for(n), 256, 0, st>>>(p, v, n);
   return cudaGetLastError();
 }
 
 cudaError_t dev_sumsq(const double* p, long long n, double* out, cudaStream_t st) {
+  note_launch();
   sumsq_kernel<<<1, 1024, 0, st>>>(p, n, out);
   return cudaGetLastError();
 }
 
 cudaError_t dev_identity_site(double* p, cudaStream_t st) {
+  note_launch();
   identity_site_kernel<<<1, 32, 0, st>>>(p);
   return cudaGetLastError();
 }

@@ -270,6 +270,7 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
   if (grid > g_max_ctas) grid = g_max_ctas;
   if (grid < 1) grid = 1;
   void* args[] = {&a};
+  note_launch();
   if ((e = cudaLaunchCooperativeKernel((void*)svd_persistent, dim3(grid), dim3(NT), args, 0, st)) !=
       cudaSuccess)
     return e;

@@ -365,6 +365,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   }
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splitk);
   if (grid.y > 65535) return cudaErrorInvalidValue;
+  note_launch();
   tc_gemm_kernel<<<grid, NTHREADS, smem, st>>>(ma, mb, p);
   return cudaGetLastError();
 }

@@ -22,6 +22,7 @@
 // factors A/B); the left half of C_E is stored [c][s][u][a'][b'] and the
 // right half [s'][u'][c''][a'][b'], so C_E = Lpart * Rpart^T is one GEMM.
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -30,8 +31,8 @@
 
 #include "../../include/xtrg.h"
 #include "common.cuh"
-#include "mixed.cuh"
 #include "mixed_ops.cuh"
+#include "subspace_split.cuh"
 #include "tc_gemm.cuh"
 
 namespace {
@@ -46,9 +47,14 @@ struct Plan {
   int L, DH, cap, cap_fat, fat_bond, capc;
   size_t n_h, n_site, n_csite, n_fat, n_pp, n_env, n_part, n_ce, n_svd, n_svd_cols, n_usbuf,
       n_obs;
+  // tensor-core path (per plane, in BF16 elements)
+  int planes;
+  size_t m_site[4], m_env, m_t1, m_lp, m_lpt, m_ct, m_part;
   size_t mixed_bytes;
   size_t total;
 };
+
+constexpr int SPLITK_MAX = 16;
 
 constexpr size_t ALIGN = 256;
 inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -80,7 +86,28 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
   p->n_svd_cols = 4 * capc;
   p->n_usbuf = capc * capc;
   p->n_obs = (size_t)DH * DH * 4 * cap * 2;
-  p->mixed_bytes = (cfg->prec == XTRG_FP64) ? 0 : mixed_workspace_bytes(L, p->cap, DH);
+  p->planes = cfg->prec == XTRG_BF16X6 ? 3 : 2;
+  {
+    const size_t c = cap, l1 = tc_ld(c), l2 = tc_ld(2 * c), lsq = tc_ld(c * c), l4 = tc_ld(4 * c);
+    p->m_site[0] = 4 * c * l1;   // rho^T layout for the first left substep
+    p->m_site[1] = 2 * c * l2;   // (u,b') x (b,t) layout for the second left substep
+    p->m_site[2] = 4 * c * l1;   // (a',t',s') x a'' layout for the first right substep
+    p->m_site[3] = 2 * c * l2;   // (b',u') x (t',b'') layout for the second right substep
+    p->m_env = c * c * l1;
+    p->m_t1 = c * 2 * c * l2;
+    p->m_lp = 4 * c * lsq;
+    p->m_lpt = c * c * l4;
+    p->m_ct = c * l4;
+    p->m_part = (size_t)SPLITK_MAX * 16 * c * c;
+    size_t pl = p->planes, mb = 0;
+    for (int k = 0; k < 4; ++k) mb += up((size_t)L * pl * p->m_site[k] * 2);
+    mb += up((size_t)(L + 1) * pl * p->m_env * 2);
+    mb += 2 * up(pl * p->m_t1 * 2) + 2 * up(pl * p->m_lp * 2) + 2 * up(pl * p->m_lpt * 2);
+    mb += up(pl * p->m_ct * 2) + up(p->m_part * 4) + ALIGN;
+    mb += up(subspace_buffer_floats(p->cap) * 4) + 2 * ALIGN;
+    mb += up(subspace_plane_elems_a(p->cap) * 2) + up(subspace_plane_elems_b(p->cap) * 2);
+    p->mixed_bytes = (cfg->prec == XTRG_FP64) ? 0 : mb;
+  }
   size_t t = 0;
   t += up((size_t)L * p->n_h * 8);          // H
   t += up((size_t)L * 4 * 8);               // identity sites
@@ -95,7 +122,7 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
   t += up(p->n_usbuf * 8);
   t += 3 * up(p->n_obs * 8);
   t += up(64 * 8);                          // scalars
-  t += up(p->mixed_bytes);
+  t += p->mixed_bytes;
   p->total = t;
   return true;
 }
@@ -116,14 +143,32 @@ struct xtrg_ctx {
   double *ob[3] = {nullptr, nullptr, nullptr};
   double* scal = nullptr;
   SvdBuffers svd{};
-  MixedCtx* mixed = nullptr;
+  // tensor-core path buffers (BF16 planes)
+  struct {
+    int P = 0, nprod = 0;
+    std::vector<__nv_bfloat16*> site[4];
+    std::vector<__nv_bfloat16*> env;
+    __nv_bfloat16 *T1 = nullptr, *T1R = nullptr, *Lp = nullptr, *Rp = nullptr, *LpT = nullptr,
+                  *RpT = nullptr, *Ct = nullptr;
+    float* part = nullptr;
+    int* err = nullptr;
+    SubspaceBuffers sb{};
+  } m;
+  bool mixed_ready = false;
   bool use_mixed = false;   // contraction arithmetic of the current product
   double lnc = 0.0, beta = 0.0;
   int nd = 0;
   bool have_rho = false;
+  bool rho_canonical = false;   // sites 1..L-1 right-orthonormal (output of init/double)
   double last_trunc = 0.0;
   double flops_contr = 0.0, flops_split = 0.0;
   long long updates = 0;
+  // profiling of the tensor-core GEMMs: event pairs resolved per product
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  double tc_flops = 0.0, tc_ms = 0.0;
+  long long tc_launches = 0;
   std::string err;
 };
 
@@ -175,11 +220,6 @@ size_t site_elems(const DevMpo& m, int i) { return (size_t)m.dims[i] * 4 * m.dim
 // ------------------------------------------------------------------ GEMMs
 xtrg_status gemm(xtrg_ctx* ctx, const GemmF64& g) {
   ctx->flops_contr += 2.0 * g.M * (double)g.N * g.K * g.batch;
-  if (ctx->use_mixed) {
-    cudaError_t e = mixed_gemm(ctx->mixed, g, ctx->st);
-    if (e != cudaSuccess) return fail(ctx, XTRG_ECUDA, "mixed gemm: %s", cudaGetErrorString(e));
-    return XTRG_OK;
-  }
   CK(gemm_f64(g, ctx->st));
   return XTRG_OK;
 }
@@ -358,8 +398,263 @@ xtrg_status normalize(xtrg_ctx* ctx, DevMpo& C, double* lns) {
   return XTRG_OK;
 }
 
+// Debug mode (environment XTRG_DEBUG=1): after each step of a product, scan
+// the FP64 result for non-finite values and name the first step that made one.
+bool debug_on() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("XTRG_DEBUG");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+xtrg_status debug_check(xtrg_ctx* ctx, const char* what, const double* p, long long n, int i) {
+  if (!debug_on() || n <= 0) return XTRG_OK;
+  CK(dev_sumsq(p, n, ctx->scal + 16, ctx->st));
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, ctx->scal + 16, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (!std::isfinite(v))
+    return fail(ctx, XTRG_ENUMERIC, "debug: %s at bond %d is not finite (sum of squares %g)", what,
+                i, v);
+  return XTRG_OK;
+}
+
 bool mixed_for_beta(const xtrg_ctx* ctx, double beta) {
-  return ctx->cfg.prec != XTRG_FP64 && ctx->mixed && beta >= ctx->cfg.beta_switch;
+  return ctx->cfg.prec != XTRG_FP64 && ctx->mixed_ready && beta >= ctx->cfg.beta_switch;
+}
+
+// ============================================================ tensor-core path
+// The doubling product A = B = rho with every contraction on tcgen05.  Layouts
+// (all operands K-major, BF16 planes, rows padded to tc_ld):
+//   site copies  sT[(t,s,a')][a]   sP[(u,b')][(b,t)]   sN[(a',t',s')][a'']   sQ[(b',u')][(t',b'')]
+//   environment  V[c][b][a]                 (left and right alike)
+//   left half    T1[c][(s,a')][(b,t)]  ->  Lp[(c,s,u)][(b',a')]
+//   right half   T1R[c''][(a',s')][(t',b'')]  ->  Rp[(s',u',c'')][(b',a')]
+//   C_E = Lp Rp^T (split-K, FP64 sum); env update V' = C^T-part x (Lp or Rp)^T.
+
+TcOperand opnd(const __nv_bfloat16* base, int P, int rows, int k, long long ld,
+               long long batch_stride, long long plane_stride, int batches) {
+  TcOperand o;
+  o.base = base; o.planes = P; o.rows = rows; o.k = k; o.ld = ld;
+  o.batch_stride = batch_stride; o.plane_stride = plane_stride; o.batches = batches;
+  return o;
+}
+
+TcOutput out_planes(__nv_bfloat16* base, int P, long long ps, Idx3 cm, Idx3 cn, long long scb) {
+  TcOutput o;
+  memset(&o, 0, sizeof o);
+  o.mode = TC_OUT_BF16P; o.bf16 = base; o.planes = P; o.plane_stride = ps;
+  o.cm = cm; o.cn = cn; o.scb = scb; o.alpha = 1.0;
+  return o;
+}
+
+#define CKM(x)                                                                              \
+  do {                                                                                      \
+    cudaError_t _e = (x);                                                                   \
+    if (_e != cudaSuccess)                                                                  \
+      return fail(ctx, XTRG_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #x,                  \
+                  cudaGetErrorString(_e));                                                  \
+  } while (0)
+
+xtrg_status tc(xtrg_ctx* ctx, const TcOperand& A, const TcOperand& B, int M, int N, int K,
+               int batch, int splitk, const TcOutput& o) {
+  const double fl = 2.0 * M * (double)N * K * batch;
+  ctx->flops_contr += fl;
+  ctx->tc_flops += fl;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->profiling) {
+    if (ctx->ev_used + 2 > ctx->ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        CKM(cudaEventCreate(&e));
+        ctx->ev.push_back(e);
+      }
+    }
+    e0 = ctx->ev[ctx->ev_used++];
+    e1 = ctx->ev[ctx->ev_used++];
+    CKM(cudaEventRecord(e0, ctx->st));
+  }
+  CKM(tc_gemm(A, B, M, N, K, batch, ctx->m.nprod, splitk, o, ctx->m.err, ctx->st));
+  if (e1) {
+    CKM(cudaEventRecord(e1, ctx->st));
+    ctx->tc_launches++;
+  }
+  return XTRG_OK;
+}
+
+// sum the recorded tensor-core GEMM intervals (the stream has been synchronised)
+xtrg_status resolve_events(xtrg_ctx* ctx) {
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float ms = 0.f;
+    CKM(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+    ctx->tc_ms += ms;
+  }
+  ctx->ev_used = 0;
+  return XTRG_OK;
+}
+
+// BF16-plane copies of rho's sites for the four substep layouts.
+xtrg_status mixed_prepare(xtrg_ctx* ctx) {
+  const DevMpo& R = ctx->rho;
+  const int P = ctx->m.P;
+  for (int i = 0; i < ctx->L; ++i) {
+    const int l = R.dims[i], r = R.dims[i + 1];
+    const double* w = R.site[i];
+    CKM(to_planes(w, idx_plain(1), idx_plain(4LL * r), 0, 4 * r, l, 1, ctx->m.site[0][i],
+                  tc_ld(l), 0, P, ctx->plan.m_site[0], ctx->st));
+    CKM(to_planes(w, idx_plain(1), idx_plain(2LL * r), 0, 2 * r, 2 * l, 1, ctx->m.site[1][i],
+                  tc_ld(2 * l), 0, P, ctx->plan.m_site[1], ctx->st));
+    CKM(to_planes(w, idx_plain(r), idx_plain(1), 0, 4 * l, r, 1, ctx->m.site[2][i], tc_ld(r), 0, P,
+                  ctx->plan.m_site[2], ctx->st));
+    CKM(to_planes(w, idx_split2(2, 4LL * r, r), idx_split2(r, 2LL * r, 1), 0, 2 * l, 2 * r, 1,
+                  ctx->m.site[3][i], tc_ld(2 * r), 0, P, ctx->plan.m_site[3], ctx->st));
+  }
+  return XTRG_OK;
+}
+
+// env slot [c][b][a] from an FP64 scalar 1 (the boundary environments)
+xtrg_status mixed_unit_env(xtrg_ctx* ctx, int slot) {
+  CK(dev_fill(ctx->scal + 8, 1.0, 1, ctx->st));
+  CKM(to_planes(ctx->scal + 8, idx_plain(0), idx_plain(0), 0, 1, 1, 1, ctx->m.env[slot], tc_ld(1),
+                0, ctx->m.P, ctx->plan.m_env, ctx->st));
+  return XTRG_OK;
+}
+
+// Lp from env[i] and site i (left half of Fig. VMPO(a), substeps 1-2)
+xtrg_status mixed_left_part(xtrg_ctx* ctx, const DevMpo& C, int i) {
+  const DevMpo& R = ctx->rho;
+  const int P = ctx->m.P;
+  const int a = R.dims[i], a2 = R.dims[i + 1], c = C.dims[i];
+  const long long ldE = tc_ld(a), ld1 = tc_ld(2 * a), ldL = tc_ld((long long)a2 * a2);
+  TcOperand Ae = opnd(ctx->m.env[i], P, a, a, ldE, (long long)a * ldE, ctx->plan.m_env, c);
+  TcOperand Bs = opnd(ctx->m.site[0][i], P, 4 * a2, a, tc_ld(a), 0, ctx->plan.m_site[0], 1);
+  TRY(tc(ctx, Ae, Bs, a, 4 * a2, a, c, 1,
+         out_planes(ctx->m.T1, P, ctx->plan.m_t1, idx_plain(2),
+                    idx_split3(2, a2, 1, (long long)a2 * ld1, ld1), 2LL * a2 * ld1)));
+  TcOperand At = opnd(ctx->m.T1, P, 2 * a2, 2 * a, ld1, 2LL * a2 * ld1, ctx->plan.m_t1, c);
+  TcOperand Bp = opnd(ctx->m.site[1][i], P, 2 * a2, 2 * a, tc_ld(2 * a), 0, ctx->plan.m_site[1], 1);
+  TRY(tc(ctx, At, Bp, 2 * a2, 2 * a2, 2 * a, c, 1,
+         out_planes(ctx->m.Lp, P, ctx->plan.m_lp, idx_split2(a2, 2 * ldL, 1),
+                    idx_split2(a2, ldL, a2), 4 * ldL)));
+  return XTRG_OK;
+}
+
+// Rp from env[j+1] and site j (right half)
+xtrg_status mixed_right_part(xtrg_ctx* ctx, const DevMpo& C, int j) {
+  const DevMpo& R = ctx->rho;
+  const int P = ctx->m.P;
+  const int a2 = R.dims[j], a3 = R.dims[j + 1], c2 = C.dims[j + 1];
+  const long long ldE = tc_ld(a3), ld2 = tc_ld(2 * a3), ldR = tc_ld((long long)a2 * a2);
+  TcOperand An = opnd(ctx->m.site[2][j], P, 4 * a2, a3, tc_ld(a3), 0, ctx->plan.m_site[2], 1);
+  TcOperand Be = opnd(ctx->m.env[j + 1], P, a3, a3, ldE, (long long)a3 * ldE, ctx->plan.m_env, c2);
+  TRY(tc(ctx, An, Be, 4 * a2, a3, a3, c2, 1,
+         out_planes(ctx->m.T1R, P, ctx->plan.m_t1, idx_split3(2, 2, 2 * ld2, a3, ld2),
+                    idx_plain(1), 2LL * a2 * ld2)));
+  TcOperand At = opnd(ctx->m.T1R, P, 2 * a2, 2 * a3, ld2, 2LL * a2 * ld2, ctx->plan.m_t1, c2);
+  TcOperand Bq = opnd(ctx->m.site[3][j], P, 2 * a2, 2 * a3, tc_ld(2 * a3), 0, ctx->plan.m_site[3], 1);
+  TRY(tc(ctx, At, Bq, 2 * a2, 2 * a2, 2 * a3, c2, 1,
+         out_planes(ctx->m.Rp, P, ctx->plan.m_lp, idx_split2(2, 1, 2LL * c2 * ldR),
+                    idx_split2(2, a2, (long long)c2 * ldR), ldR)));
+  return XTRG_OK;
+}
+
+// new environment at slot from a C site (FP64) and the Lp or Rp planes:
+//   left:  V'[c'][b'][a'] = sum_{(c,s,u)} C_i[(c,s,u)][c'] Lp[(c,s,u)][(b',a')]
+//   right: V'[c'][b'][a'] = sum_{(s',u',c'')} C_j[c'][(s',u',c'')] Rp[(s',u',c'')][(b',a')]
+xtrg_status mixed_env(xtrg_ctx* ctx, const double* Csite, int kout, int kin, bool left,
+                      const __nv_bfloat16* part, int a, int slot) {
+  const int P = ctx->m.P;
+  const long long ab = (long long)a * a, ldP = tc_ld(ab), ldK = tc_ld(kin), ldE = tc_ld(a);
+  // C^T-part [c'][k]: left reads C_i[k][c'], right reads C_j[c'][k]
+  CKM(to_planes(Csite, left ? idx_plain(1) : idx_plain(kin), left ? idx_plain(kout) : idx_plain(1),
+                0, kout, kin, 1, ctx->m.Ct, ldK, 0, P, ctx->plan.m_ct, ctx->st));
+  __nv_bfloat16* T = left ? ctx->m.LpT : ctx->m.RpT;
+  CKM(transpose_planes(part, ldP, (int)ab, kin, T, ldK, P, ctx->plan.m_lp, ctx->plan.m_lpt,
+                       ctx->st));
+  TcOperand Ac = opnd(ctx->m.Ct, P, kout, kin, ldK, 0, ctx->plan.m_ct, 1);
+  TcOperand Bt = opnd(T, P, (int)ab, kin, ldK, 0, ctx->plan.m_lpt, 1);
+  return tc(ctx, Ac, Bt, kout, (int)ab, kin, 1, 1,
+            out_planes(ctx->m.env[slot], P, ctx->plan.m_env, idx_plain((long long)a * ldE),
+                       idx_split2(a, ldE, 1), 0));
+}
+
+// C_E = Lp Rp^T (FP32 accumulation, split-K partials summed in FP64)
+xtrg_status mixed_ce(xtrg_ctx* ctx, int m, int n, int a2) {
+  const int P = ctx->m.P;
+  const long long K = (long long)a2 * a2, ld = tc_ld(K);
+  const int kb = (int)((K + 63) / 64);
+  const int tiles = ((m + 127) / 128) * ((n + 127) / 128);
+  int splitk = (2 * 152 + tiles - 1) / tiles;
+  if (splitk > SPLITK_MAX) splitk = SPLITK_MAX;
+  if (splitk > kb / 4) splitk = kb / 4;
+  if (splitk < 1) splitk = 1;
+  TcOperand Al = opnd(ctx->m.Lp, P, m, (int)K, ld, 0, ctx->plan.m_lp, 1);
+  TcOperand Br = opnd(ctx->m.Rp, P, n, (int)K, ld, 0, ctx->plan.m_lp, 1);
+  TcOutput o;
+  memset(&o, 0, sizeof o);
+  o.mode = TC_OUT_PARTIAL; o.f32 = ctx->m.part; o.alpha = 1.0;
+  TRY(tc(ctx, Al, Br, m, n, (int)K, 1, splitk, o));
+  CKM(reduce_partials(ctx->m.part, splitk, (long long)m * n, ctx->CE, ctx->st));
+  return XTRG_OK;
+}
+
+xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
+  const int L = ctx->L;
+  const DevMpo& R = ctx->rho;
+  const int kcap = dstar < ctx->cap ? dstar : ctx->cap;
+  CKM(cudaMemsetAsync(ctx->m.err, 0, sizeof(int), ctx->st));
+  TRY(mixed_unit_env(ctx, 0));
+  TRY(mixed_unit_env(ctx, L));
+  for (int j = L - 1; j >= 1; --j) {
+    TRY(mixed_right_part(ctx, C, j));
+    TRY(mixed_env(ctx, C.site[j], C.dims[j], 4 * C.dims[j + 1], false, ctx->m.Rp, R.dims[j], j));
+  }
+  double maxdisc = 0.0;
+  for (int s = 0; s < sweeps; ++s) {
+    const bool last = s == sweeps - 1;
+    for (int dir = 0; dir < 2; ++dir) {
+      for (int step = 0; step < L - 1; ++step) {
+        const int i = dir == 0 ? step : L - 2 - step;
+        TRY(mixed_left_part(ctx, C, i));
+        TRY(mixed_right_part(ctx, C, i + 1));
+        const int m = 4 * C.dims[i], n = 4 * C.dims[i + 2];
+        TRY(mixed_ce(ctx, m, n, R.dims[i + 1]));
+        TRY(debug_check(ctx, "C_E", ctx->CE, (long long)m * n, i));
+        // keep k = min(D*, m, n): the FP32-level C_E has no FP64-exact numerical rank
+        int k = kcap < m ? kcap : m;
+        k = k < n ? k : n;
+        double disc = 0.0;
+        const unsigned long long seed =
+            0x243F6A8885A308D3ull ^ ((unsigned long long)ctx->nd << 40) ^ (unsigned long long)ctx->updates;
+        if (dir == 0) {
+          CKM(subspace_split(ctx->CE, m, n, k, 1, C.site[i + 1], C.dims[i + 1], C.site[i],
+                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc));
+        } else {
+          CKM(subspace_split(ctx->CE, m, n, k, 0, C.site[i], C.dims[i + 1], C.site[i],
+                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc));
+        }
+        C.dims[i + 1] = k;
+        TRY(debug_check(ctx, "left factor", C.site[i], (long long)m * k, i));
+        TRY(debug_check(ctx, "right factor", C.site[i + 1], (long long)k * n, i));
+        ctx->flops_split += 2.0 * m * (double)n * k * 2 + 3.0 * (2.0 * (dir == 0 ? m : n) * k * k);
+        if (last && disc > maxdisc) maxdisc = disc;
+        if (dir == 0)
+          TRY(mixed_env(ctx, C.site[i], k, m, true, ctx->m.Lp, R.dims[i + 1], i + 1));
+        else
+          TRY(mixed_env(ctx, C.site[i + 1], k, n, false, ctx->m.Rp, R.dims[i + 1], i + 1));
+        ctx->updates++;
+      }
+    }
+  }
+  int h = 0;
+  CKM(cudaMemcpyAsync(&h, ctx->m.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CKM(cudaStreamSynchronize(ctx->st));
+  if (h) return fail(ctx, XTRG_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
+  TRY(resolve_events(ctx));
+  ctx->last_trunc = maxdisc;
+  return XTRG_OK;
 }
 
 // ------------------------------------------------------------ transfers
@@ -453,6 +748,7 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
       (int)cfg->prec < 0 || (int)cfg->prec > 2)
     return XTRG_EINVAL;
   if (!dev_workspace || ((uintptr_t)dev_workspace % ALIGN) != 0) return XTRG_EINVAL;
+  if (cfg->prec != XTRG_FP64 && cfg->dstar > 256) return XTRG_EINVAL;  // tensor-core truncation bound
   Plan p;
   if (!plan_sizes(Hm->L, max_bond(Hm), cfg, &p)) return XTRG_EINVAL;
   if (workspace_bytes < p.total) return XTRG_ENOMEM;
@@ -492,8 +788,50 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
        ctx->svd.kept && ctx->svd.stats && ctx->usbuf && ctx->ob[0] && ctx->ob[1] && ctx->ob[2] &&
        ctx->scal;
   if (ok && p.mixed_bytes) {
-    char* mb = carve(ctx, p.mixed_bytes);
-    ok = mb && mixed_create(&ctx->mixed, mb, p.mixed_bytes, ctx->L, ctx->cap, ctx->DH) == cudaSuccess;
+    const int P = p.planes, L = ctx->L;
+    ctx->m.P = P;
+    ctx->m.nprod = P == 3 ? 6 : 3;
+    for (int k = 0; k < 4 && ok; ++k) {
+      __nv_bfloat16* b = (__nv_bfloat16*)carve(ctx, (size_t)L * P * p.m_site[k] * 2);
+      ok = b != nullptr;
+      for (int i = 0; ok && i < L; ++i) ctx->m.site[k].push_back(b + (size_t)i * P * p.m_site[k]);
+    }
+    __nv_bfloat16* eb = (__nv_bfloat16*)carve(ctx, (size_t)(L + 1) * P * p.m_env * 2);
+    ok = ok && eb;
+    for (int i = 0; ok && i <= L; ++i) ctx->m.env.push_back(eb + (size_t)i * P * p.m_env);
+    ctx->m.T1 = (__nv_bfloat16*)carve(ctx, P * p.m_t1 * 2);
+    ctx->m.T1R = (__nv_bfloat16*)carve(ctx, P * p.m_t1 * 2);
+    ctx->m.Lp = (__nv_bfloat16*)carve(ctx, P * p.m_lp * 2);
+    ctx->m.Rp = (__nv_bfloat16*)carve(ctx, P * p.m_lp * 2);
+    ctx->m.LpT = (__nv_bfloat16*)carve(ctx, P * p.m_lpt * 2);
+    ctx->m.RpT = (__nv_bfloat16*)carve(ctx, P * p.m_lpt * 2);
+    ctx->m.Ct = (__nv_bfloat16*)carve(ctx, P * p.m_ct * 2);
+    ctx->m.part = (float*)carve(ctx, p.m_part * 4);
+    ctx->m.err = (int*)carve(ctx, 16);
+    {
+      const size_t c = p.cap, mm = 4 * c;
+      float* f = (float*)carve(ctx, subspace_buffer_floats(p.cap) * 4);
+      ok = ok && f;
+      if (f) {
+        ctx->m.sb.CE32 = f; f += mm * mm;
+        ctx->m.sb.Q = f; f += mm * c;
+        ctx->m.sb.Y = f; f += mm * c;
+        ctx->m.sb.G = f; f += c * c;
+        ctx->m.sb.L = f; f += c * c;
+        ctx->m.sb.out = f; f += mm * mm;
+        ctx->m.sb.scal = f;
+      }
+      ctx->m.sb.dscal = (double*)carve(ctx, 16);
+      ctx->m.sb.pa = (__nv_bfloat16*)carve(ctx, subspace_plane_elems_a(p.cap) * 2);
+      ctx->m.sb.pb = (__nv_bfloat16*)carve(ctx, subspace_plane_elems_b(p.cap) * 2);
+      ctx->m.sb.psa = (long long)(subspace_plane_elems_a(p.cap) / 3);
+      ctx->m.sb.psb = (long long)(subspace_plane_elems_b(p.cap) / 3);
+      ctx->m.sb.err = ctx->m.err;
+      ok = ok && ctx->m.sb.dscal && ctx->m.sb.pa && ctx->m.sb.pb;
+    }
+    ok = ok && ctx->m.T1 && ctx->m.T1R && ctx->m.Lp && ctx->m.Rp && ctx->m.LpT && ctx->m.RpT &&
+         ctx->m.Ct && ctx->m.part && ctx->m.err;
+    ctx->mixed_ready = ok;
   }
   if (!ok) {
     delete ctx;
@@ -557,6 +895,7 @@ extern "C" xtrg_status xtrg_init(xtrg_ctx* ctx) {
   ctx->beta = ctx->cfg.tau0;
   ctx->nd = 0;
   ctx->have_rho = true;
+  ctx->rho_canonical = true;
   ctx->last_trunc = 0.0;
   return XTRG_OK;
 }
@@ -565,20 +904,29 @@ extern "C" xtrg_status xtrg_double(xtrg_ctx* ctx) {
   if (!ctx) return XTRG_EINVAL;
   if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "xtrg_double before xtrg_init");
   ctx->use_mixed = mixed_for_beta(ctx, ctx->beta);
-  if (ctx->use_mixed) {
-    cudaError_t e = mixed_prepare(ctx->mixed, ctx->rho.dims.data(), ctx->rho.site.data(), ctx->st);
-    if (e != cudaSuccess) return fail(ctx, XTRG_ECUDA, "mixed prepare: %s", cudaGetErrorString(e));
+  if (ctx->rho_canonical) {
+    // rho from init/double is already right-canonical: right-canonicalising
+    // it again changes only the gauge, so the guess is a plain copy
+    ctx->C.dims = ctx->rho.dims;
+    for (int i = 0; i < ctx->L; ++i)
+      CK(cudaMemcpyAsync(ctx->C.site[i], ctx->rho.site[i], sizeof(double) * site_elems(ctx->rho, i),
+                         cudaMemcpyDeviceToDevice, ctx->st));
+  } else {
+    TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, ctx->C));
   }
-  TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, ctx->C));
-  xtrg_status s = compress(ctx, ctx->rho, ctx->rho, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps);
-  ctx->use_mixed = false;
-  if (s != XTRG_OK) return s;
+  if (ctx->use_mixed) {
+    TRY(mixed_prepare(ctx));
+    TRY(compress_mixed(ctx, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+  } else {
+    TRY(compress(ctx, ctx->rho, ctx->rho, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+  }
   double lns = 0.0;
   TRY(normalize(ctx, ctx->C, &lns));
   std::swap(ctx->rho, ctx->C);
   ctx->lnc = 2.0 * ctx->lnc + lns;
   ctx->beta *= 2.0;
   ctx->nd++;
+  ctx->rho_canonical = true;
   return XTRG_OK;
 }
 
@@ -637,7 +985,8 @@ extern "C" xtrg_status xtrg_get_state(xtrg_ctx* ctx, int* bond_dims, double* con
   return XTRG_OK;
 }
 
-extern "C" xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* r, double lnc, double beta) {
+extern "C" xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* r, double lnc, double beta,
+                                      int right_canonical) {
   if (!ctx) return XTRG_EINVAL;
   if (check_mpo(r, ctx->cap) != XTRG_OK || r->L != ctx->L)
     return fail(ctx, XTRG_EINVAL, "state MPO has the wrong length or a bond above %d", ctx->cap);
@@ -650,14 +999,25 @@ extern "C" xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* r, double l
   ctx->lnc = lnc;
   ctx->beta = beta;
   ctx->have_rho = true;
+  ctx->rho_canonical = right_canonical != 0;
   return XTRG_OK;
 }
 
-extern "C" xtrg_status xtrg_counters(const xtrg_ctx* ctx, double* cf, double* sf, long long* upd) {
+extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
+  if (!ctx || !o) return XTRG_EINVAL;
+  o->contraction_flops = ctx->flops_contr;
+  o->split_flops = ctx->flops_split;
+  o->tc_flops = ctx->tc_flops;
+  o->tc_ms = ctx->tc_ms;
+  o->two_site_updates = ctx->updates;
+  o->tc_launches = ctx->tc_launches;
+  o->kernel_launches = (long long)__atomic_load_n(&g_xtrg_launches, __ATOMIC_RELAXED);
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_set_profiling(xtrg_ctx* ctx, int on) {
   if (!ctx) return XTRG_EINVAL;
-  if (cf) *cf = ctx->flops_contr;
-  if (sf) *sf = ctx->flops_split;
-  if (upd) *upd = ctx->updates;
+  ctx->profiling = on != 0;
   return XTRG_OK;
 }
 
@@ -730,6 +1090,6 @@ extern "C" const char* xtrg_last_error(const xtrg_ctx* ctx) {
 
 extern "C" void xtrg_destroy(xtrg_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->mixed) mixed_destroy(ctx->mixed);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }

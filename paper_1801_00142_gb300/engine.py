@@ -54,11 +54,14 @@ class XTRG:
     def get_state(self):
         return _lib.xtrg_get_state(self.ctx, self.L)
 
-    def set_state(self, sites, lnc, beta):
-        _lib.xtrg_set_state(self.ctx, sites, lnc, beta)
+    def set_state(self, sites, lnc, beta, right_canonical=False):
+        _lib.xtrg_set_state(self.ctx, sites, lnc, beta, right_canonical)
 
     def counters(self):
-        return _lib.xtrg_counters(self.ctx)
+        return _lib.xtrg_get_stats(self.ctx)
+
+    def set_profiling(self, on=True):
+        _lib.xtrg_set_profiling(self.ctx, on)
 
     def close(self):
         if getattr(self, "ctx", None):

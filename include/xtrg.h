@@ -167,6 +167,23 @@ xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int
                          int batch, int planes, int nprod, int splitk, void* workspace,
                          size_t workspace_bytes, void* cuda_stream);
 
+/* xtrg_tc_gemm for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a service of this library.  Same arguments,
+ * results and precision as xtrg_tc_gemm, without the workspace: the scratch
+ * (operand planes, partial sums, an error flag) lives in one file-scope
+ * device array of 16 MiB that every GPU loading this library holds until
+ * the process exits.  Sizes must satisfy
+ *   r(planes*batch*M*ld*2) + r(planes*batch*N*ld*2) + r(splitk*batch*M*N*4) + 256 <= 16 MiB,
+ * with ld = K rounded up to a multiple of 8 and r() rounding up to 256 bytes;
+ * larger sizes return XTRG_ENOMEM and do nothing.  The call allocates no
+ * device memory.  The first call on a device looks up the array's device
+ * address (with that device current), so make it before any stream capture.
+ * Every call uses the same array: calls that overlap on the GPU race, so
+ * order them (one stream, or events).  Uses the current device and
+ * synchronises the given stream. */
+xtrg_status xtrg_tc_gemm_static(const double* A, const double* B, double* C, int M, int N, int K,
+                                int batch, int planes, int nprod, int splitk, void* cuda_stream);
+
 const char* xtrg_last_error(const xtrg_ctx* ctx);
 
 /* Free host bookkeeping.  The workspace stays the caller's. */

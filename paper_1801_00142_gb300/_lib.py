@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "XTRG_OK", 1: "XTRG_EINVAL", 2: "XTRG_ENOMEM", 3: "XTRG_ECUDA
 SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "xtrg_trace",
            "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_get_stats",
            "xtrg_set_profiling",
-           "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm"]
+           "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm",
+           "xtrg_tc_gemm_static"]
 
 
 class xtrg_mpo(C.Structure):
@@ -99,6 +100,8 @@ def _load():
     lib.xtrg_tc_gemm_workspace_bytes.argtypes = [C.c_int] * 6
     lib.xtrg_tc_gemm.restype = C.c_int
     lib.xtrg_tc_gemm.argtypes = [P, P, P] + [C.c_int] * 7 + [P, C.c_size_t, P]
+    lib.xtrg_tc_gemm_static.restype = C.c_int
+    lib.xtrg_tc_gemm_static.argtypes = [P, P, P] + [C.c_int] * 7 + [P]
     return lib
 
 
@@ -204,6 +207,13 @@ def xtrg_tc_gemm(A_ptr, B_ptr, C_ptr, M, N, K, batch, planes, nprod, splitk, ws_
                          C.c_void_p(stream))
     if s != XTRG_OK:
         raise XtrgError(s, "xtrg_tc_gemm")
+
+
+def xtrg_tc_gemm_static(A_ptr, B_ptr, C_ptr, M, N, K, batch, planes, nprod, splitk, stream):
+    """xtrg_tc_gemm without a workspace (scratch in a fixed device array);
+    returns the status code unchanged so callers can see XTRG_ENOMEM."""
+    return int(LIB.xtrg_tc_gemm_static(C.c_void_p(A_ptr), C.c_void_p(B_ptr), C.c_void_p(C_ptr),
+                                       M, N, K, batch, planes, nprod, splitk, C.c_void_p(stream)))
 
 
 def xtrg_last_error(ctx) -> str:

@@ -26,8 +26,8 @@ def _run(w, H):
 
 def run(w):
     """Oracle rows; for truncated runs also the oracle's own sensitivity: the
-    change of each row when the nonzero entries of H are perturbed by
-    1e-14 relative noise (several truncated results are equally optimal when
+    largest change of each row over three seeded perturbations of the
+    nonzero entries of H by 1e-14 relative noise (several truncated results are equally optimal when
     D* cuts through a degenerate set of singular values, so a parity bar
     below this sensitivity would be meaningless)."""
     import numpy as np
@@ -37,11 +37,15 @@ def run(w):
     secs = time.time() - t
     truncated = any(r.get("trunc", 0.0) > 1e-24 for r in rows)
     if truncated:
-        rng = np.random.default_rng(7)
-        Hp = [h * (1.0 + 1e-14 * rng.standard_normal(h.shape)) for h in H]
-        pert = _run(w, Hp)
-        for r, q in zip(rows, pert):
-            r["sens"] = {k: abs(r[k] - q[k]) for k in ("lnZ", "u", "c")}
+        for r in rows:
+            r["sens"] = {"lnZ": 0.0, "u": 0.0, "c": 0.0}
+        for seed in (7, 8, 9):
+            rng = np.random.default_rng(seed)
+            Hp = [h * (1.0 + 1e-14 * rng.standard_normal(h.shape)) for h in H]
+            pert = _run(w, Hp)
+            for r, q in zip(rows, pert):
+                for k in ("lnZ", "u", "c"):
+                    r["sens"][k] = max(r["sens"][k], abs(r[k] - q[k]))
     return {"workload": w.__dict__, "rows": rows, "oracle_seconds": secs,
             "truncated": truncated}
 

@@ -143,6 +143,7 @@ typedef struct {
   long long two_site_updates;
   long long tc_launches;     /* tensor-core GEMM launches (only while profiling)     */
   long long kernel_launches; /* kernels launched by this library, all contexts      */
+  long long exact_split_fallbacks; /* tensor-core-path updates that took the exact FP64 split */
 } xtrg_stats;
 
 /* Counters since creation (kernel_launches: since the library was loaded). */

@@ -1,5 +1,5 @@
 // Truncation of the tensor-core path: one warm-started subspace step with
-// shifted CholeskyQR3 orthonormalisation, in FP32.
+// block Gram-Schmidt orthonormalisation.
 //
 // The two-site update keeps the dominant rank-k subspace of C_E (Fig.
 // VMPO(d)).  The FP64 path computes it exactly by Jacobi SVD; here, where
@@ -10,12 +10,19 @@
 // C_{i+1} (right-canonical guess, or V^T of the previous right-to-left pass),
 // padded with pseudo-random columns when the bond grows.  The tiny random
 // term eta R keeps every column of Y away from exact zero; directions it adds
-// carry weight below eta^2 relative.  orth() is block classical Gram-Schmidt
-// with reorthogonalisation (panels of 32 columns, three projection passes
-// against the earlier panels as FP32 GEMMs, then three in-panel passes in
-// shared memory): unlike Cholesky-based QR it does not square the condition
-// number, so columns without weight in C_E become arbitrary orthonormal
-// completions instead of breaking the factorisation.
+// carry weight below eta^2 relative.
+//
+// orth() is block classical Gram-Schmidt over panels of 32 columns: two FP32
+// projection passes against the earlier panels, then CholeskyQR2 inside the
+// panel with the 32 x 32 Gram and its Cholesky factor in FP64.  Columns whose
+// Cholesky pivot sits at the FP64 noise floor carry no weight and are set to
+// zero instead of being divided by that pivot.  It runs as one persistent
+// cooperative kernel: every CTA keeps its slab of rows in shared memory,
+// reductions over rows go through per-CTA partials in global memory (summed
+// in a fixed order, so results are deterministic), and phases are separated
+// by bounded grid barriers.  The caller checks max |U^T U - I| over the live
+// columns and takes the exact split when the FP32 projections lost
+// orthogonality (steep, rank-deficient spectra).
 #include <math.h>
 
 #include "common.cuh"
@@ -101,62 +108,180 @@ __global__ void sumsq_f64_kernel(const double* __restrict__ a, long long n, doub
   }
 }
 
-// In-panel orthonormalisation: columns [j0, j0+w) of Y (rows x k, row-major)
-// against each other, three passes per column, then normalisation.  One CTA;
-// the panel lives in shared memory.
 constexpr int PANEL = 32;
-constexpr int PSTR = PANEL + 1;   // padded row stride: conflict-free shared-memory columns
+constexpr int ORTH_NT = 256;
+constexpr int ROWS_PER_CTA = 8;
+constexpr int MAX_K = 256;
+constexpr long long ORTH_SPIN_LIMIT = 1LL << 22;
 
-__global__ void __launch_bounds__(1024) panel_orth_kernel(float* __restrict__ Y, int rows, int k,
-                                                          int j0, int w) {
-  extern __shared__ float V[];    // V[r * PSTR + c]
-  __shared__ float dots[PANEL];
-  __shared__ float red[32];
-  const int tid = threadIdx.x, lane = tid % 32, wid = tid / 32, nw = blockDim.x / 32;
-  for (int e = tid; e < rows * w; e += blockDim.x) {
-    const int r = e / w, c = e % w;
-    V[r * PSTR + c] = Y[(long long)r * k + j0 + c];
+struct OrthArgs {
+  float* Y;          // rows x k, row-major
+  int rows, k;
+  float* part;       // [G][MAX_K * PANEL] per-CTA partial sums
+  float* red;        // [MAX_K * PANEL] reduced sums
+  double* partd;     // [G][PANEL * PANEL] per-CTA partial Grams (FP64)
+  double* redd;      // [PANEL * PANEL] reduced Gram (FP64)
+  unsigned* bar;     // [0] arrivals, [1] generation
+  int* status;       // 0 ok, 1 barrier timeout
+};
+
+// grid barrier with a bounded wait (false: timed out, every CTA leaves)
+__device__ bool orth_barrier(const OrthArgs& a) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vb = a.bar;
+    volatile int* stp = a.status;
+    if (*stp) {
+      ok = 0;
+    } else {
+      const unsigned gen = vb[1];
+      __threadfence();
+      const unsigned arrived = atomicAdd(a.bar, 1u);
+      if (arrived == gridDim.x - 1) {
+        vb[0] = 0;
+        __threadfence();
+        atomicAdd(a.bar + 1, 1u);
+      } else {
+        long long it = 0;
+        while (vb[1] == gen) {
+          if (++it > ORTH_SPIN_LIMIT || *stp) {
+            atomicExch(a.status, 1);
+            ok = 0;
+            break;
+          }
+          if (it > 64) __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
   }
   __syncthreads();
-  for (int c = 0; c < w; ++c) {
-    for (int pass = 0; pass < 3; ++pass) {
-      if (c > 0) {
-        // dots[c'] = <v_c', v_c> for c' < c, one warp per c'
-        for (int cp = wid; cp < c; cp += nw) {
-          float s = 0.f;
-          for (int r = lane; r < rows; r += 32) s = fmaf(V[r * PSTR + cp], V[r * PSTR + c], s);
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0) dots[cp] = s;
-        }
-        __syncthreads();
-        for (int r = tid; r < rows; r += blockDim.x) {
-          float v = V[r * PSTR + c];
-          for (int cp = 0; cp < c; ++cp) v = fmaf(-dots[cp], V[r * PSTR + cp], v);
-          V[r * PSTR + c] = v;
-        }
-        __syncthreads();
-      }
-    }
+  return ok != 0;
+}
+
+// sum of the per-CTA partials of n entries into a.red: one warp per entry,
+// lane l adds partials l, l+32, ... and a fixed shuffle tree combines the
+// lanes (fixed order, so the result is deterministic)
+__device__ void reduce_partials_grid(const OrthArgs& a, int n) {
+  const int G = gridDim.x, lane = threadIdx.x % 32;
+  const int warp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int nwarps = G * (blockDim.x / 32);
+  for (int e = warp; e < n; e += nwarps) {
     float s = 0.f;
-    for (int r = tid; r < rows; r += blockDim.x) s = fmaf(V[r * PSTR + c], V[r * PSTR + c], s);
+    for (int g = lane; g < G; g += 32) s += a.part[(long long)g * MAX_K * PANEL + e];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[wid] = s;
-    __syncthreads();
-    if (tid == 0) {
-      float t = 0.f;
-      for (int i = 0; i < nw; ++i) t += red[i];
-      dots[0] = t > 0.f ? rsqrtf(t) : 0.f;
-    }
-    __syncthreads();
-    const float inv = dots[0];
-    for (int r = tid; r < rows; r += blockDim.x) V[r * PSTR + c] *= inv;
-    __syncthreads();
-  }
-  for (int e = tid; e < rows * w; e += blockDim.x) {
-    const int r = e / w, c = e % w;
-    Y[(long long)r * k + j0 + c] = V[r * PSTR + c];
+    if (lane == 0) a.red[e] = s;
   }
 }
+
+__device__ void reduce_partials_grid_f64(const OrthArgs& a, int n) {
+  const int G = gridDim.x, lane = threadIdx.x % 32;
+  const int warp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int nwarps = G * (blockDim.x / 32);
+  for (int e = warp; e < n; e += nwarps) {
+    double s = 0.0;
+    for (int g = lane; g < G; g += 32) s += a.partd[(long long)g * PANEL * PANEL + e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) a.redd[e] = s;
+  }
+}
+
+__global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
+  __shared__ float Ys[ROWS_PER_CTA][MAX_K + 1];
+  __shared__ float Ss[MAX_K * PANEL];
+  __shared__ double Ld[PANEL][PANEL + 1];
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * ROWS_PER_CTA;
+  const int nr = min(ROWS_PER_CTA, a.rows - r0);
+  const int k = a.k;
+  float* mypart = a.part + (long long)blockIdx.x * MAX_K * PANEL;
+  for (int e = tid; e < ROWS_PER_CTA * k; e += ORTH_NT) {
+    const int r = e / k, c = e % k;
+    Ys[r][c] = r < nr ? a.Y[(long long)(r0 + r) * k + c] : 0.f;
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < k; j0 += PANEL) {
+    const int w = min(PANEL, k - j0);
+    // ---- two projection passes against columns [0, j0)
+    for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
+      for (int e = tid; e < j0 * w; e += ORTH_NT) {
+        const int j = e / w, c = e % w;
+        float s = 0.f;
+        for (int r = 0; r < nr; ++r) s = fmaf(Ys[r][j], Ys[r][j0 + c], s);
+        mypart[e] = s;
+      }
+      if (!orth_barrier(a)) return;
+      reduce_partials_grid(a, j0 * w);
+      if (!orth_barrier(a)) return;
+      for (int e = tid; e < j0 * w; e += ORTH_NT) Ss[e] = a.red[e];
+      __syncthreads();
+      for (int e = tid; e < nr * w; e += ORTH_NT) {
+        const int r = e / w, c = e % w;
+        float v = Ys[r][j0 + c];
+        for (int j = 0; j < j0; ++j) v = fmaf(-Ys[r][j], Ss[j * w + c], v);
+        Ys[r][j0 + c] = v;
+      }
+      // the next partials are written only after this CTA passed the next
+      // barrier's arrival, and every CTA read a.red before arriving there
+      if (!orth_barrier(a)) return;
+    }
+    // ---- CholeskyQR2 inside the panel with an FP64 Gram and Cholesky;
+    // columns whose pivot is at the FP64 noise floor carry no weight and are
+    // set to zero (dead) instead of being divided by that pivot
+    for (int pass = 0; pass < 2; ++pass) {
+      double* mypd = a.partd + (long long)blockIdx.x * PANEL * PANEL;
+      for (int e = tid; e < w * w; e += ORTH_NT) {
+        const int c = e / w, d = e % w;
+        double s = 0.0;
+        for (int r = 0; r < nr; ++r) s = fma((double)Ys[r][j0 + c], (double)Ys[r][j0 + d], s);
+        mypd[e] = s;
+      }
+      if (!orth_barrier(a)) return;
+      reduce_partials_grid_f64(a, w * w);
+      if (!orth_barrier(a)) return;
+      for (int e = tid; e < w * w; e += ORTH_NT) Ld[e / w][e % w] = a.redd[e];
+      __syncthreads();
+      if (tid < 32) {
+        const int lane = tid;
+        double dmax = 0.0;
+        for (int c = 0; c < w; ++c) dmax = fmax(dmax, Ld[c][c]);
+        const double thr = 1e-13 * dmax;
+        for (int j = 0; j < w; ++j) {
+          const double pj = Ld[j][j];
+          const bool dead = !(pj > thr) || !(dmax > 0.0);
+          const double d = dead ? 0.0 : sqrt(pj);
+          __syncwarp();
+          if (lane == j) Ld[j][j] = d;
+          if (lane > j && lane < w) Ld[lane][j] = dead ? 0.0 : Ld[lane][j] / d;
+          __syncwarp();
+          if (lane > j && lane < w)
+            for (int c = j + 1; c <= lane; ++c) Ld[lane][c] -= Ld[lane][j] * Ld[c][j];
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // rows <- rows L^{-T} (dead columns -> 0)
+      for (int r = tid; r < nr; r += ORTH_NT) {
+        double x[PANEL];
+        for (int c = 0; c < w; ++c) {
+          double v = (double)Ys[r][j0 + c];
+          for (int d = 0; d < c; ++d) v = fma(-x[d], Ld[c][d], v);
+          x[c] = Ld[c][c] > 0.0 ? v / Ld[c][c] : 0.0;
+        }
+        for (int c = 0; c < w; ++c) Ys[r][j0 + c] = (float)x[c];
+      }
+      if (!orth_barrier(a)) return;
+    }
+  }
+  for (int e = tid; e < nr * k; e += ORTH_NT) {
+    const int r = e / k, c = e % k;
+    a.Y[(long long)(r0 + r) * k + c] = Ys[r][c];
+  }
+}
+
+int g_orth_max_ctas = 0;
 
 GemmF32 g32(int M, int N, int K, const float* A, Idx3 am, Idx3 ak, const float* B, Idx3 bk,
             Idx3 bn, float* C, Idx3 cm, Idx3 cn) {
@@ -175,34 +300,29 @@ GemmF32 g32(int M, int N, int K, const float* A, Idx3 am, Idx3 ak, const float* 
     if (_e != cudaSuccess) return _e;          \
   } while (0)
 
-// Y (rows x k, row-major FP32) <- orthonormal basis of its column space
-// (block classical Gram-Schmidt, three passes).  S: k x PANEL scratch.
-cudaError_t block_cgs(float* Y, int rows, int k, float* S, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    RET(cudaFuncSetAttribute(panel_orth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             1028 * PSTR * (int)sizeof(float)));
-    attr = true;
+// Y (rows x k, row-major FP32) <- orthonormal basis of its column space.
+cudaError_t orth_check(const float* Q, int rows, int k, const SubspaceBuffers& b, cudaStream_t st);
+
+cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
+  if (k > MAX_K) return cudaErrorInvalidValue;
+  const int G = (rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+  if (g_orth_max_ctas == 0) {
+    int dev = 0, sms = 0, per = 0;
+    RET(cudaGetDevice(&dev));
+    RET(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RET(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, orth_persistent, ORTH_NT, 0));
+    g_orth_max_ctas = sms * per;
   }
-  if (rows > 1028) return cudaErrorInvalidValue;
-  for (int j0 = 0; j0 < k; j0 += PANEL) {
-    const int w = k - j0 < PANEL ? k - j0 : PANEL;
-    for (int pass = 0; pass < 3 && j0 > 0; ++pass) {
-      // S = Q[:, :j0]^T Y[:, j0:j0+w]
-      RET(gemm_f32(g32(j0, w, rows, Y, idx_plain(1), idx_plain(k), Y + j0, idx_plain(k),
-                       idx_plain(1), S, idx_plain(w), idx_plain(1)),
-                   st));
-      // Y[:, j0:j0+w] -= Q[:, :j0] S
-      GemmF32 g = g32(rows, w, j0, Y, idx_plain(k), idx_plain(1), S, idx_plain(w), idx_plain(1),
-                      Y + j0, idx_plain(k), idx_plain(1));
-      g.alpha = -1.0;
-      g.beta = 1.0;
-      RET(gemm_f32(g, st));
-    }
-    note_launch();
-    panel_orth_kernel<<<1, 1024, (size_t)rows * PSTR * sizeof(float), st>>>(Y, rows, k, j0, w);
-    RET(cudaGetLastError());
-  }
+  if (G > g_orth_max_ctas || G > b.orth_max_ctas) return cudaErrorInvalidValue;
+  OrthArgs a;
+  a.Y = Y; a.rows = rows; a.k = k;
+  a.part = b.orth_part; a.red = b.orth_red;
+  a.partd = b.orth_partd; a.redd = b.orth_redd;
+  a.bar = b.orth_bar; a.status = (int*)(b.orth_bar + 2);
+  RET(cudaMemsetAsync(b.orth_bar, 0, 4 * sizeof(unsigned), st));
+  void* args[] = {&a};
+  note_launch();
+  RET(cudaLaunchCooperativeKernel((void*)orth_persistent, dim3(G), dim3(ORTH_NT), args, 0, st));
   return cudaSuccess;
 }
 
@@ -240,22 +360,57 @@ cudaError_t tc_product(const View& a, const View& b, int M, int N, int K, float*
   o.alpha = 1.0;
   return tc_gemm(A, B, M, N, K, 1, 6, 1, o, buf.err, st);
 }
+
+// max over live columns of |Q^T Q - I| (dead columns, norm < 1/2, are skipped)
+// into b.dscal[2] (as FP64).  Q^T Q by the tensor cores, 6 products.
+__global__ void orth_defect_kernel(const float* __restrict__ G, int k, double* out) {
+  __shared__ float red[32];
+  float mx = 0.f;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e % k;
+    const float gi = G[(long long)i * k + i], gj = G[(long long)j * k + j];
+    if (gi < 0.5f || gj < 0.5f) continue;
+    const float d = fabsf(G[e] - (i == j ? 1.f : 0.f));
+    mx = fmaxf(mx, d != d ? 1e30f : d);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t = fmaxf(t, red[i]);
+    *out = (double)t;
+  }
+}
+
+cudaError_t orth_check(const float* Q, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
+  RET(tc_product(View{nullptr, Q, idx_plain(1), idx_plain(k)},
+                 View{nullptr, Q, idx_plain(1), idx_plain(k)}, k, k, rows, b.out, k, b, st));
+  note_launch();
+  orth_defect_kernel<<<1, 1024, 0, st>>>(b.out, k, b.dscal + 2);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t subspace_buffer_floats(int cap) {
   const size_t m = 4 * (size_t)cap;
-  return m * m /*CE32*/ + m * cap /*Q*/ + m * cap /*Y*/ + (size_t)cap * cap * 2 /*G, L*/ +
-         m * m /*out*/ + 64;
+  const size_t G = (m + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+  return m * cap /*Q*/ + m * cap /*Y*/ + m * m /*out*/ + G * MAX_K * PANEL /*orth partials*/ +
+         MAX_K * PANEL /*orth reduced*/ + 64 /*scal*/ + 2 * G * PANEL * PANEL /*FP64 partial Grams*/ +
+         2 * PANEL * PANEL /*FP64 Gram*/ + 64;
 }
+
+int subspace_orth_ctas(int cap) { return (4 * cap + ROWS_PER_CTA - 1) / ROWS_PER_CTA; }
 
 cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
                            const double* warm, int kold, double* left, double* right,
                            unsigned long long seed, const SubspaceBuffers& b, cudaStream_t st,
-                           double* discarded) {
+                           double* discarded, double* orth_defect) {
   if (k > 256 || k > m || k > n) return cudaErrorInvalidValue;
   const long long mn = (long long)m * n;
   // ||C_E||^2 (FP64)
-  RET(cudaMemsetAsync(b.dscal, 0, 2 * sizeof(double), st));
+  RET(cudaMemsetAsync(b.dscal, 0, 3 * sizeof(double), st));
   note_launch();
   sumsq_f64_kernel<<<grid_for(mn) < 304 ? grid_for(mn) : 304, 256, 0, st>>>(CE, mn, b.dscal);
   RET(cudaGetLastError());
@@ -275,7 +430,8 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
     add_noise_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.Y, (long long)m * k, eta,
                                                                  seed + 7);
     RET(cudaGetLastError());
-    RET(block_cgs(b.Y, m, k, b.G, st));
+    RET(block_cgs(b.Y, m, k, b, st));
+    RET(orth_check(b.Y, m, k, b, st));
     // C_i = U (m x k); C_{i+1} = U^T C_E (k x n)
     note_launch();
     copy_f2d_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.Y, (long long)m * k, left);
@@ -297,7 +453,8 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
     add_noise_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(b.Y, (long long)n * k, eta,
                                                                  seed + 7);
     RET(cudaGetLastError());
-    RET(block_cgs(b.Y, n, k, b.G, st));
+    RET(block_cgs(b.Y, n, k, b, st));
+    RET(orth_check(b.Y, n, k, b, st));
     // C_{i+1} = V^T (k x n); C_i = C_E V (m x k)
     note_launch();
     transpose_f2d_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(b.Y, n, k, right);
@@ -315,9 +472,10 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
   sumsq_f64_kernel<<<grid_for(nc) < 304 ? grid_for(nc) : 304, 256, 0, st>>>(centre, nc,
                                                                             b.dscal + 1);
   RET(cudaGetLastError());
-  double kept = 0.0;
-  RET(cudaMemcpyAsync(&kept, b.dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  double h[2] = {0.0, 0.0};
+  RET(cudaMemcpyAsync(h, b.dscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   RET(cudaStreamSynchronize(st));
-  *discarded = tot > 0.0 ? fmax(0.0, 1.0 - kept / tot) : 0.0;
+  *discarded = tot > 0.0 ? fmax(0.0, 1.0 - h[0] / tot) : 0.0;
+  *orth_defect = h[1];
   return cudaSuccess;
 }

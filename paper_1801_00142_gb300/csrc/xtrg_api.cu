@@ -104,7 +104,7 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
     mb += up((size_t)(L + 1) * pl * p->m_env * 2);
     mb += 2 * up(pl * p->m_t1 * 2) + 2 * up(pl * p->m_lp * 2) + 2 * up(pl * p->m_lpt * 2);
     mb += up(pl * p->m_ct * 2) + up(p->m_part * 4) + ALIGN;
-    mb += up(subspace_buffer_floats(p->cap) * 4) + 2 * ALIGN;
+    mb += up(subspace_buffer_floats(p->cap) * 4) + 3 * ALIGN;
     mb += up(subspace_plane_elems_a(p->cap) * 2) + up(subspace_plane_elems_b(p->cap) * 2);
     p->mixed_bytes = (cfg->prec == XTRG_FP64) ? 0 : mb;
   }
@@ -169,6 +169,11 @@ struct xtrg_ctx {
   size_t ev_used = 0;
   double tc_flops = 0.0, tc_ms = 0.0;
   long long tc_launches = 0;
+  std::vector<int> ev_tag;             // call site of each event pair
+  double tag_ms[8] = {0}, tag_flops[8] = {0};
+  long long tag_n[8] = {0};
+  int cur_tag = 0;
+  long long fallbacks = 0;   // tensor-core path updates that used the exact split
   std::string err;
 };
 
@@ -474,6 +479,9 @@ xtrg_status tc(xtrg_ctx* ctx, const TcOperand& A, const TcOperand& B, int M, int
     }
     e0 = ctx->ev[ctx->ev_used++];
     e1 = ctx->ev[ctx->ev_used++];
+    ctx->ev_tag.push_back(ctx->cur_tag);
+    ctx->tag_flops[ctx->cur_tag] += fl;
+    ctx->tag_n[ctx->cur_tag]++;
     CKM(cudaEventRecord(e0, ctx->st));
   }
   CKM(tc_gemm(A, B, M, N, K, batch, ctx->m.nprod, splitk, o, ctx->m.err, ctx->st));
@@ -490,8 +498,10 @@ xtrg_status resolve_events(xtrg_ctx* ctx) {
     float ms = 0.f;
     CKM(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
     ctx->tc_ms += ms;
+    if (i / 2 < ctx->ev_tag.size()) ctx->tag_ms[ctx->ev_tag[i / 2]] += ms;
   }
   ctx->ev_used = 0;
+  ctx->ev_tag.clear();
   return XTRG_OK;
 }
 
@@ -528,11 +538,13 @@ xtrg_status mixed_left_part(xtrg_ctx* ctx, const DevMpo& C, int i) {
   const int P = ctx->m.P;
   const int a = R.dims[i], a2 = R.dims[i + 1], c = C.dims[i];
   const long long ldE = tc_ld(a), ld1 = tc_ld(2 * a), ldL = tc_ld((long long)a2 * a2);
+  ctx->cur_tag = 1;
   TcOperand Ae = opnd(ctx->m.env[i], P, a, a, ldE, (long long)a * ldE, ctx->plan.m_env, c);
   TcOperand Bs = opnd(ctx->m.site[0][i], P, 4 * a2, a, tc_ld(a), 0, ctx->plan.m_site[0], 1);
   TRY(tc(ctx, Ae, Bs, a, 4 * a2, a, c, 1,
          out_planes(ctx->m.T1, P, ctx->plan.m_t1, idx_plain(2),
                     idx_split3(2, a2, 1, (long long)a2 * ld1, ld1), 2LL * a2 * ld1)));
+  ctx->cur_tag = 2;
   TcOperand At = opnd(ctx->m.T1, P, 2 * a2, 2 * a, ld1, 2LL * a2 * ld1, ctx->plan.m_t1, c);
   TcOperand Bp = opnd(ctx->m.site[1][i], P, 2 * a2, 2 * a, tc_ld(2 * a), 0, ctx->plan.m_site[1], 1);
   TRY(tc(ctx, At, Bp, 2 * a2, 2 * a2, 2 * a, c, 1,
@@ -547,11 +559,13 @@ xtrg_status mixed_right_part(xtrg_ctx* ctx, const DevMpo& C, int j) {
   const int P = ctx->m.P;
   const int a2 = R.dims[j], a3 = R.dims[j + 1], c2 = C.dims[j + 1];
   const long long ldE = tc_ld(a3), ld2 = tc_ld(2 * a3), ldR = tc_ld((long long)a2 * a2);
+  ctx->cur_tag = 1;
   TcOperand An = opnd(ctx->m.site[2][j], P, 4 * a2, a3, tc_ld(a3), 0, ctx->plan.m_site[2], 1);
   TcOperand Be = opnd(ctx->m.env[j + 1], P, a3, a3, ldE, (long long)a3 * ldE, ctx->plan.m_env, c2);
   TRY(tc(ctx, An, Be, 4 * a2, a3, a3, c2, 1,
          out_planes(ctx->m.T1R, P, ctx->plan.m_t1, idx_split3(2, 2, 2 * ld2, a3, ld2),
                     idx_plain(1), 2LL * a2 * ld2)));
+  ctx->cur_tag = 2;
   TcOperand At = opnd(ctx->m.T1R, P, 2 * a2, 2 * a3, ld2, 2LL * a2 * ld2, ctx->plan.m_t1, c2);
   TcOperand Bq = opnd(ctx->m.site[3][j], P, 2 * a2, 2 * a3, tc_ld(2 * a3), 0, ctx->plan.m_site[3], 1);
   TRY(tc(ctx, At, Bq, 2 * a2, 2 * a2, 2 * a3, c2, 1,
@@ -573,6 +587,7 @@ xtrg_status mixed_env(xtrg_ctx* ctx, const double* Csite, int kout, int kin, boo
   __nv_bfloat16* T = left ? ctx->m.LpT : ctx->m.RpT;
   CKM(transpose_planes(part, ldP, (int)ab, kin, T, ldK, P, ctx->plan.m_lp, ctx->plan.m_lpt,
                        ctx->st));
+  ctx->cur_tag = 4;
   TcOperand Ac = opnd(ctx->m.Ct, P, kout, kin, ldK, 0, ctx->plan.m_ct, 1);
   TcOperand Bt = opnd(T, P, (int)ab, kin, ldK, 0, ctx->plan.m_lpt, 1);
   return tc(ctx, Ac, Bt, kout, (int)ab, kin, 1, 1,
@@ -590,6 +605,7 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, int m, int n, int a2) {
   if (splitk > SPLITK_MAX) splitk = SPLITK_MAX;
   if (splitk > kb / 4) splitk = kb / 4;
   if (splitk < 1) splitk = 1;
+  ctx->cur_tag = 3;
   TcOperand Al = opnd(ctx->m.Lp, P, m, (int)K, ld, 0, ctx->plan.m_lp, 1);
   TcOperand Br = opnd(ctx->m.Rp, P, n, (int)K, ld, 0, ctx->plan.m_lp, 1);
   TcOutput o;
@@ -625,15 +641,25 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
         // keep k = min(D*, m, n): the FP32-level C_E has no FP64-exact numerical rank
         int k = kcap < m ? kcap : m;
         k = k < n ? k : n;
-        double disc = 0.0;
+        double disc = 0.0, defect = 0.0;
         const unsigned long long seed =
             0x243F6A8885A308D3ull ^ ((unsigned long long)ctx->nd << 40) ^ (unsigned long long)ctx->updates;
         if (dir == 0) {
           CKM(subspace_split(ctx->CE, m, n, k, 1, C.site[i + 1], C.dims[i + 1], C.site[i],
-                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc));
+                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc, &defect));
         } else {
           CKM(subspace_split(ctx->CE, m, n, k, 0, C.site[i], C.dims[i + 1], C.site[i],
-                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc));
+                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc, &defect));
+        }
+        if (!(defect <= 1e-4)) {
+          // the FP32 orthonormalisation lost orthogonality (steep or rank-
+          // deficient spectrum): take the exact FP64 Jacobi split instead
+          SvdResult r;
+          TRY(split(ctx, ctx->CE, m, n, k, dir == 0 ? SPLIT_RIGHT : SPLIT_LEFT, C.site[i],
+                    C.site[i + 1], &r));
+          k = r.k;
+          disc = r.discarded;
+          ctx->fallbacks++;
         }
         C.dims[i + 1] = k;
         TRY(debug_check(ctx, "left factor", C.site[i], (long long)m * k, i));
@@ -813,14 +839,19 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
       float* f = (float*)carve(ctx, subspace_buffer_floats(p.cap) * 4);
       ok = ok && f;
       if (f) {
-        ctx->m.sb.CE32 = f; f += mm * mm;
+        const size_t G = (size_t)subspace_orth_ctas(p.cap);
         ctx->m.sb.Q = f; f += mm * c;
         ctx->m.sb.Y = f; f += mm * c;
-        ctx->m.sb.G = f; f += c * c;
-        ctx->m.sb.L = f; f += c * c;
         ctx->m.sb.out = f; f += mm * mm;
-        ctx->m.sb.scal = f;
+        ctx->m.sb.orth_part = f; f += G * 256 * 32;
+        ctx->m.sb.orth_red = f; f += 256 * 32;
+        ctx->m.sb.scal = f; f += 64;
+        ctx->m.sb.orth_partd = (double*)f; f += 2 * G * 32 * 32;
+        ctx->m.sb.orth_redd = (double*)f; f += 2 * 32 * 32;
+        ctx->m.sb.orth_max_ctas = (int)G;
       }
+      ctx->m.sb.orth_bar = (unsigned*)carve(ctx, 16);
+      ok = ok && ctx->m.sb.orth_bar;
       ctx->m.sb.dscal = (double*)carve(ctx, 16);
       ctx->m.sb.pa = (__nv_bfloat16*)carve(ctx, subspace_plane_elems_a(p.cap) * 2);
       ctx->m.sb.pb = (__nv_bfloat16*)carve(ctx, subspace_plane_elems_b(p.cap) * 2);
@@ -1012,6 +1043,7 @@ extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
   o->two_site_updates = ctx->updates;
   o->tc_launches = ctx->tc_launches;
   o->kernel_launches = (long long)__atomic_load_n(&g_xtrg_launches, __ATOMIC_RELAXED);
+  o->exact_split_fallbacks = ctx->fallbacks;
   return XTRG_OK;
 }
 
@@ -1090,6 +1122,16 @@ extern "C" const char* xtrg_last_error(const xtrg_ctx* ctx) {
 
 extern "C" void xtrg_destroy(xtrg_ctx* ctx) {
   if (!ctx) return;
+  const char* pt = getenv("XTRG_PROFILE_TAGS");
+  if (pt && pt[0] == '1') {
+    static const char* names[8] = {"other", "substep1 (env x site)", "substep2 (x site)",
+                                   "C_E (split-K)", "env update", "", "", ""};
+    for (int t = 0; t < 8; ++t)
+      if (ctx->tag_n[t])
+        fprintf(stderr, "xtrg tc %-24s launches %8lld  %10.1f ms  %8.1f TFLOP/s alg\n", names[t],
+                ctx->tag_n[t], ctx->tag_ms[t],
+                ctx->tag_ms[t] > 0 ? ctx->tag_flops[t] / ctx->tag_ms[t] / 1e9 : 0.0);
+  }
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }

@@ -161,6 +161,21 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def aggregate(ms_local, steps_local, dist=None, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's timed
+    interval (max over ranks) and the sum of all ranks' steps.  Returns
+    (ms_max, steps_total, value in steps/s)."""
+    import torch
+    ms, steps = float(ms_local), float(steps_local)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        n = torch.tensor([steps], dtype=torch.float64, device=device)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        ms, steps = float(t.item()), float(n.item())
+    return ms, steps, steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- GPU path
 def run_native(args):
     import torch
@@ -213,11 +228,7 @@ def run_native(args):
     clk = clocks.stop()
     s1 = eng.counters()
     eng.set_profiling(False)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, steps_total, value = aggregate(e0.elapsed_time(e1), args.steps, dist, dev)
 
     # end to end through the C ABI with host buffers: upload rho, double,
     # observables, download rho, every step
@@ -241,8 +252,6 @@ def run_native(args):
         return
     peaks, src = measured_peaks()
     nprod = {"bf16x6": 6, "bf16x3": 3}.get(args.prec, 0)
-    steps_total = args.steps * ws
-    value = steps_total / (ms / 1e3)
     tc_ms = s1["tc_ms"] - s0["tc_ms"]
     tc_fl = s1["tc_flops"] - s0["tc_flops"]
     contr = s1["contraction_flops"] - s0["contraction_flops"]

@@ -1,6 +1,7 @@
 // tcgen05 / TMA GEMM kernel (see tc_gemm.cuh).
 //
-// CTA tile 128 x 128 (M x N), K-block 64 BF16 = one 128-byte swizzle row.
+// CTA tile 128 x 128 (M x N), K-block 64 BF16 = one 128-byte swizzle row;
+// persistent CTAs (one per SM) with the accumulator double-buffered in TMEM.
 // Warp 0: TMA producer (one elected thread); warp 1: MMA issuer (one elected
 // thread, 4 x UMMA_K=16 per K-block and product); warp 2: tensor-memory
 // allocation; warps 4-7: epilogue (tcgen05.ld 32x32b, lane quarter = warp % 4).
@@ -148,6 +149,11 @@ __device__ __forceinline__ void store_out(const TcOutput& o, long long off, floa
   }
 }
 
+// Persistent kernel: every CTA walks the output tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (tile order: n fastest, then m, then batch x
+// split).  The accumulator is double-buffered in tensor memory (2 x 128
+// columns), so the epilogue of one tile overlaps the main loop of the next;
+// the operand stage ring continues across tiles.
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const KParams p) {
@@ -158,22 +164,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int stage_bytes = (p.pa_planes + p.pb_planes) * TILE_BYTES;
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
   uint64_t* empty = full + S;
-  uint64_t* done = empty + S;
+  uint64_t* acc_full = empty + S;     // [2]
+  uint64_t* acc_empty = acc_full + 2; // [2]
+  uint64_t* done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  long long* col_off_all = (long long*)(tmem_slot + 2);   // [4][BN] per-warp column offsets
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int z = blockIdx.z;
-  const int bidx = z / p.splitk, split = z % p.splitk;
-  const int kb_begin = split * p.kb_per;
-  int kb_end = kb_begin + p.kb_per;
-  if (kb_end > p.kb_total) kb_end = p.kb_total;
-  const int nk = kb_end > kb_begin ? kb_end - kb_begin : 0;
+  const int tiles_n = (p.N + BN - 1) / BN, tiles_m = (p.M + BM - 1) / BM;
+  const int tiles = tiles_n * tiles_m * p.batch * p.splitk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -181,7 +189,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(BN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -192,81 +200,126 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    const int ba = p.a_batched ? bidx : 0, bb = p.b_batched ? bidx : 0;
-    int issued = 0;
+    long long g = 0;   // k-blocks issued by this CTA
     bool ok = true;
-    for (int i = 0; i < nk && ok; ++i) {
-      const int s = i % S;
-      if (i >= S) ok = mbar_wait(&empty[s], ((i / S) - 1) & 1, p.err);
-      if (!ok) break;
-      uint8_t* st = smem + s * stage_bytes;
-      mbar_expect_tx(&full[s], stage_bytes);
-      const int k0 = (kb_begin + i) * BK;
-      for (int q = 0; q < p.pa_planes; ++q)
-        tma_load_4d(st + q * TILE_BYTES, &mapA, &full[s], k0, m0, ba, q);
-      for (int q = 0; q < p.pb_planes; ++q)
-        tma_load_4d(st + (p.pa_planes + q) * TILE_BYTES, &mapB, &full[s], k0, n0, bb, q);
-      ++issued;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
+      const int bidx = z / p.splitk, split = z % p.splitk;
+      const int kb_begin = split * p.kb_per;
+      const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
+      const int ba = p.a_batched ? bidx : 0, bb = p.b_batched ? bidx : 0;
+      for (int kb = kb_begin; kb < kb_end && ok; ++kb, ++g) {
+        const int s = (int)(g % S);
+        if (g >= S) ok = mbar_wait(&empty[s], (uint32_t)(((g / S) - 1) & 1), p.err);
+        if (!ok) break;
+        uint8_t* st = smem + s * stage_bytes;
+        mbar_expect_tx(&full[s], stage_bytes);
+        const int k0 = kb * BK;
+        for (int q = 0; q < p.pa_planes; ++q)
+          tma_load_4d(st + q * TILE_BYTES, &mapA, &full[s], k0, mt * BM, ba, q);
+        for (int q = 0; q < p.pb_planes; ++q)
+          tma_load_4d(st + (p.pa_planes + q) * TILE_BYTES, &mapB, &full[s], k0, nt * BN, bb, q);
+      }
     }
     // drain: every load issued must have landed before the CTA may exit
-    for (int i = (issued > S ? issued - S : 0); i < issued; ++i)
-      mbar_wait(&full[i % S], (i / S) & 1, p.err);
+    for (long long i = (g > S ? g - S : 0); i < g; ++i)
+      mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), p.err);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16_128x128();
+    long long g = 0;
+    int j = 0;   // tiles of this CTA
     bool ok = true;
-    int consumed = 0;
-    for (int i = 0; i < nk && ok; ++i) {
-      const int s = i % S;
-      ok = mbar_wait(&full[s], (i / S) & 1, p.err);
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++j) {
+      const int z = t / (tiles_n * tiles_m);
+      const int split = z % p.splitk;
+      const int kb_begin = split * p.kb_per;
+      const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
+      const int buf = j & 1;
+      if (j >= 2) ok = mbar_wait(&acc_empty[buf], (uint32_t)(((j >> 1) - 1) & 1), p.err);
       if (!ok) break;
       fence_after();
-      const uint32_t base = smem_u32(smem + s * stage_bytes);
-      for (int pr = 0; pr < p.nprod; ++pr) {
-        const uint32_t a_addr = base + p.prod_a[pr] * TILE_BYTES;
-        const uint32_t b_addr = base + (p.pa_planes + p.prod_b[pr]) * TILE_BYTES;
+      const uint32_t dcol = tmem + (uint32_t)(buf * BN);
+      for (int kb = kb_begin; kb < kb_end && ok; ++kb, ++g) {
+        const int s = (int)(g % S);
+        ok = mbar_wait(&full[s], (uint32_t)((g / S) & 1), p.err);
+        if (!ok) break;
+        fence_after();
+        const uint32_t base = smem_u32(smem + s * stage_bytes);
+        for (int pr = 0; pr < p.nprod; ++pr) {
+          const uint32_t a_addr = base + p.prod_a[pr] * TILE_BYTES;
+          const uint32_t b_addr = base + (p.pa_planes + p.prod_b[pr]) * TILE_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          // advance 16 BF16 = 32 B along K inside the swizzled 128-B row
-          uint64_t da = smem_desc(a_addr) + (uint64_t)(kk * 2);
-          uint64_t db = smem_desc(b_addr) + (uint64_t)(kk * 2);
-          mma_bf16(tmem, da, db, idesc, (i > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            // advance 16 BF16 = 32 B along K inside the swizzled 128-B row
+            uint64_t da = smem_desc(a_addr) + (uint64_t)(kk * 2);
+            uint64_t db = smem_desc(b_addr) + (uint64_t)(kk * 2);
+            mma_bf16(dcol, da, db, idesc, (kb > kb_begin || pr > 0 || kk > 0) ? 1u : 0u);
+          }
         }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
-      ++consumed;
+      if (ok) mma_commit(&acc_full[buf]);
     }
     // the done barrier tracks completion of every MMA issued so far
     mma_commit(done);
   } else if (warp >= 4) {
-    // ---------------- epilogue
+    // ---------------- epilogue (4 warps; warp % 4 selects the TMEM lane quarter)
     const int q = warp % 4;
-    const bool ok = mbar_wait(done, 0, p.err);
-    fence_after();
-    const int m = m0 + q * 32 + lane;
     const TcOutput& o = p.out;
-    if (ok) {
+    long long* col_off = col_off_all + q * BN;
+    int j = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+      const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
+      const int bidx = z / p.splitk, split = z % p.splitk;
+      const int kb_begin = split * p.kb_per;
+      const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
+      const int n0 = nt * BN, m0 = mt * BM;
+      const int buf = j & 1;
+      // column offsets of this tile, computed once per warp (the 3-level views
+      // need divisions); warp-private, so no barrier across warps is needed
+      __syncwarp();
+      for (int cc = lane; cc < BN; cc += 32) {
+        const int n = n0 + cc;
+        col_off[cc] = (o.mode == TC_OUT_PARTIAL || n >= p.N) ? (long long)n : idx_off(o.cn, n);
+      }
+      __syncwarp();
+      if (!mbar_wait(&acc_full[buf], (uint32_t)((j >> 1) & 1), p.err)) break;
+      fence_after();
+      const int m = m0 + q * 32 + lane;
+      const bool row_ok = m < p.M;
+      long long om = 0;
+      float* dstp = nullptr;
+      if (o.mode == TC_OUT_PARTIAL)
+        dstp = o.f32 + (((long long)split * p.batch + bidx) * p.M + (row_ok ? m : 0)) * (long long)p.N;
+      else if (row_ok)
+        om = bidx * o.scb + idx_off(o.cm, m);
+      const float alpha = (float)o.alpha;
       for (int c = 0; c < BN; c += 32) {
         float v[32];
-        if (nk > 0) {
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (kb_end > kb_begin) {
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), v);
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = 0.f;
+          for (int jj = 0; jj < 32; ++jj) v[jj] = 0.f;
         }
-        if (m >= p.M) continue;
+        if (c == BN - 32) {
+          // every TMEM load of this warp is complete: hand the buffer back
+          fence_before();
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf]))
+                         : "memory");
+        }
+        if (!row_ok) continue;
         if (o.mode == TC_OUT_PARTIAL) {
-          float* dst = o.f32 + (((long long)split * p.batch + bidx) * p.M + m) * (long long)p.N;
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (n0 + c + j < p.N) dst[n0 + c + j] = v[j];
+          for (int jj = 0; jj < 32; ++jj)
+            if (n0 + c + jj < p.N) dstp[n0 + c + jj] = v[jj];
         } else {
-          const long long om = bidx * o.scb + idx_off(o.cm, m);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c + j;
-            if (n < p.N) store_out(o, om + idx_off(o.cn, n), (float)o.alpha * v[j]);
-          }
+          for (int jj = 0; jj < 32; ++jj)
+            if (n0 + c + jj < p.N) store_out(o, om + col_off[c + jj], alpha * v[jj]);
         }
       }
     }
@@ -274,8 +327,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   fence_before();
   __syncthreads();
   if (warp == 2) {
+    // all MMAs of this CTA have completed before its tensor memory is freed
+    if (lane == 0) mbar_wait(done, 0, p.err);
+    __syncwarp();
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN)
                  : "memory");
   }
 }
@@ -355,7 +411,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   cudaError_t e;
   if ((e = make_map(&ma, A)) != cudaSuccess) return e;
   if ((e = make_map(&mb, B)) != cudaSuccess) return e;
-  const int smem = S * stage_bytes + 1024 + (2 * S + 2) * 8 + 64;
+  const int smem = S * stage_bytes + 1024 + (2 * S + 5) * 8 + 8 + 4 * BN * 8 + 64;
   static bool attr_done = false;
   if (!attr_done) {
     if ((e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -363,8 +419,17 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
       return e;
     attr_done = true;
   }
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splitk);
-  if (grid.y > 65535) return cudaErrorInvalidValue;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+  }
+  const long long tiles =
+      (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * (long long)batch * splitk;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)(tiles < sms ? tiles : sms));
   note_launch();
   tc_gemm_kernel<<<grid, NTHREADS, smem, st>>>(ma, mb, p);
   return cudaGetLastError();

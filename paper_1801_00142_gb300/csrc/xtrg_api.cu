@@ -54,7 +54,7 @@ struct Plan {
   size_t total;
 };
 
-constexpr int SPLITK_MAX = 16;
+constexpr int SPLITK_MAX = 32;
 
 constexpr size_t ALIGN = 256;
 inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -601,7 +601,11 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, int m, int n, int a2) {
   const long long K = (long long)a2 * a2, ld = tc_ld(K);
   const int kb = (int)((K + 63) / 64);
   const int tiles = ((m + 127) / 128) * ((n + 127) / 128);
+  // enough splits to fill the GPU twice over, and each FP32 accumulation
+  // chain at most 32 K-blocks (2048 terms) long; the partials are summed in FP64
   int splitk = (2 * 152 + tiles - 1) / tiles;
+  const int by_len = (kb + 31) / 32;
+  if (splitk < by_len) splitk = by_len;
   if (splitk > SPLITK_MAX) splitk = SPLITK_MAX;
   if (splitk > kb / 4) splitk = kb / 4;
   if (splitk < 1) splitk = 1;

@@ -39,6 +39,17 @@ DESC = ("Heisenberg XXX chain, L=64 open, J=1, Delta=1, D*=256, 4 sweeps/doublin
         "tau0=2^-12 doubled to beta=64; the last steps of that schedule are timed")
 
 
+def set_workload(L, dstar):
+    """Replace the timed chain by a smaller one of the same family (for
+    profiler captures that must stay small); the defaults are the headline
+    workload."""
+    global W, DESC
+    if (L, dstar) != (W.L, W.dstar):
+        W = W.with_(name=f"xxx_L{L}_D{dstar}", L=L, dstar=dstar)
+        DESC = (f"Heisenberg XXX chain, L={L} open, J=1, Delta=1, D*={dstar}, 4 sweeps/doubling, "
+                f"tau0=2^-12 doubled to beta=64 (profiling case)")
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -287,8 +298,6 @@ def run_native(args):
            "observables_last": {k: rows[-1][k] for k in ("beta", "f", "u", "c", "max_bond")}}
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(2)
-    elif not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(2)
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -304,7 +313,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-region", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop")
+    ap.add_argument("--L", type=int, default=W.L,
+                    help="chain length (smaller chains only for profiler captures)")
+    ap.add_argument("--dstar", type=int, default=W.dstar,
+                    help="bond cap D* (smaller caps only for profiler captures)")
     args = ap.parse_args()
+    set_workload(args.L, args.dstar)
     if args.impl == "reference":
         run_reference(args)
     else:

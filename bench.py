@@ -295,7 +295,7 @@ def run_native(args):
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": s1["kernel_launches"] - s0["kernel_launches"],
            "exact_split_fallbacks": s1["exact_split_fallbacks"] - s0["exact_split_fallbacks"],
-           "observables_last": {k: rows[-1][k] for k in ("beta", "f", "u", "c", "max_bond")}}
+           "observables_last": {k: rows[-1][k] for k in ("beta", "lnZ", "f", "u", "max_bond")}}
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(2)
     print(json.dumps(out))

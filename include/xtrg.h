@@ -80,6 +80,11 @@ typedef struct {
   xtrg_precision prec;  /* contraction arithmetic for beta >= beta_switch     */
   double beta_switch;   /* doublings that start below this beta run in FP64   */
   double svd_rel_tol;   /* singular values <= svd_rel_tol * sigma_max are dropped (numerically zero) */
+  int keep_parts;       /* tensor-core path: 0 = each two-site update builds both
+                           halves of its environment (Fig. VMPO(a)); 1 = the halves
+                           of every bond stay resident in device memory, so each
+                           update builds one (about 2 L x 4 D*^3 x planes BF16
+                           elements more workspace)                            */
 } xtrg_config;
 
 typedef struct {

@@ -36,7 +36,8 @@ class xtrg_mpo(C.Structure):
 class xtrg_config(C.Structure):
     _fields_ = [("tau0", C.c_double), ("order", C.c_int), ("dstar", C.c_int),
                 ("sweeps", C.c_int), ("init_sweeps", C.c_int), ("prec", C.c_int),
-                ("beta_switch", C.c_double), ("svd_rel_tol", C.c_double)]
+                ("beta_switch", C.c_double), ("svd_rel_tol", C.c_double),
+                ("keep_parts", C.c_int)]
 
 
 class xtrg_obs(C.Structure):
@@ -121,10 +122,11 @@ class MpoArgs:
 
 
 def make_config(tau0, order, dstar, sweeps, init_sweeps=None, prec="fp64", beta_switch=0.0,
-                svd_rel_tol=1e-15):
+                svd_rel_tol=1e-15, keep_parts=True):
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     return xtrg_config(float(tau0), int(order), int(dstar), int(sweeps),
-                       int(init_sweeps or sweeps), p, float(beta_switch), float(svd_rel_tol))
+                       int(init_sweeps or sweeps), p, float(beta_switch), float(svd_rel_tol),
+                       int(bool(keep_parts)))
 
 
 def _check(ctx, status):

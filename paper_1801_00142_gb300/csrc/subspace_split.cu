@@ -161,36 +161,51 @@ __device__ bool orth_barrier(const OrthArgs& a) {
   return ok != 0;
 }
 
-// sum of the per-CTA partials of n entries into a.red: one warp per entry,
-// lane l adds partials l, l+32, ... and a fixed shuffle tree combines the
-// lanes (fixed order, so the result is deterministic)
-__device__ void reduce_partials_grid(const OrthArgs& a, int n) {
-  const int G = gridDim.x, lane = threadIdx.x % 32;
-  const int warp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int nwarps = G * (blockDim.x / 32);
-  for (int e = warp; e < n; e += nwarps) {
-    float s = 0.f;
-    for (int g = lane; g < G; g += 32) s += a.part[(long long)g * MAX_K * PANEL + e];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) a.red[e] = s;
+// Sum of the per-CTA partials of n entries into a.red (a.redd): each CTA
+// takes chunks of 32 consecutive entries; its warps split the G partials
+// (coalesced 128-byte rows), and a fixed-order sum over the warps in shared
+// memory combines them, so the result is deterministic.  The loop bounds
+// depend on blockIdx only, so every thread of a CTA takes the same branches
+// through the __syncthreads().
+// scratch: ORTH_NT values of T in shared memory (the caller's Ss, which is
+// not live during a reduction)
+template <typename T>
+__device__ void reduce_partials_grid_t(const T* __restrict__ part, long long part_stride,
+                                       T* __restrict__ red, int n, T* scratch) {
+  T (*red_s)[32] = reinterpret_cast<T (*)[32]>(scratch);
+  const int G = gridDim.x, lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  constexpr int NW = ORTH_NT / 32;
+  for (int e0 = blockIdx.x * 32; e0 < n; e0 += gridDim.x * 32) {
+    const int e = e0 + lane;
+    T s = T(0);
+    if (e < n) {
+#pragma unroll 4
+      for (int g = w; g < G; g += NW) s += part[(long long)g * part_stride + e];
+    }
+    red_s[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && e < n) {
+      T t = T(0);
+#pragma unroll
+      for (int q = 0; q < NW; ++q) t += red_s[q][lane];
+      red[e] = t;
+    }
+    __syncthreads();
   }
 }
 
-__device__ void reduce_partials_grid_f64(const OrthArgs& a, int n) {
-  const int G = gridDim.x, lane = threadIdx.x % 32;
-  const int warp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int nwarps = G * (blockDim.x / 32);
-  for (int e = warp; e < n; e += nwarps) {
-    double s = 0.0;
-    for (int g = lane; g < G; g += 32) s += a.partd[(long long)g * PANEL * PANEL + e];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) a.redd[e] = s;
-  }
+__device__ void reduce_partials_grid(const OrthArgs& a, int n, float* scratch) {
+  reduce_partials_grid_t<float>(a.part, (long long)MAX_K * PANEL, a.red, n, scratch);
+}
+
+__device__ void reduce_partials_grid_f64(const OrthArgs& a, int n, float* scratch) {
+  reduce_partials_grid_t<double>(a.partd, (long long)PANEL * PANEL, a.redd, n,
+                                 reinterpret_cast<double*>(scratch));
 }
 
 __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
   __shared__ float Ys[ROWS_PER_CTA][MAX_K + 1];
-  __shared__ float Ss[MAX_K * PANEL];
+  __shared__ __align__(16) float Ss[MAX_K * PANEL];
   __shared__ double Ld[PANEL][PANEL + 1];
   const int tid = threadIdx.x;
   const int r0 = blockIdx.x * ROWS_PER_CTA;
@@ -213,7 +228,7 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         mypart[e] = s;
       }
       if (!orth_barrier(a)) return;
-      reduce_partials_grid(a, j0 * w);
+      reduce_partials_grid(a, j0 * w, Ss);
       if (!orth_barrier(a)) return;
       for (int e = tid; e < j0 * w; e += ORTH_NT) Ss[e] = a.red[e];
       __syncthreads();
@@ -223,9 +238,10 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         for (int j = 0; j < j0; ++j) v = fmaf(-Ys[r][j], Ss[j * w + c], v);
         Ys[r][j0 + c] = v;
       }
-      // the next partials are written only after this CTA passed the next
-      // barrier's arrival, and every CTA read a.red before arriving there
-      if (!orth_barrier(a)) return;
+      // No barrier here: the next reduction writes a.red only after the
+      // next phase's first barrier, which every CTA reaches after its copy
+      // of a.red; and the partials are rewritten only after the barrier that
+      // ended this reduction.
     }
     // ---- CholeskyQR2 inside the panel with an FP64 Gram and Cholesky;
     // columns whose pivot is at the FP64 noise floor carry no weight and are
@@ -239,7 +255,7 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         mypd[e] = s;
       }
       if (!orth_barrier(a)) return;
-      reduce_partials_grid_f64(a, w * w);
+      reduce_partials_grid_f64(a, w * w, Ss);
       if (!orth_barrier(a)) return;
       for (int e = tid; e < w * w; e += ORTH_NT) Ld[e / w][e % w] = a.redd[e];
       __syncthreads();
@@ -272,7 +288,7 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         }
         for (int c = 0; c < w; ++c) Ys[r][j0 + c] = (float)x[c];
       }
-      if (!orth_barrier(a)) return;
+      // (no barrier: the same argument as for the projection passes)
     }
   }
   for (int e = tid; e < nr * k; e += ORTH_NT) {

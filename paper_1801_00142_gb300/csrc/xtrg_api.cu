@@ -102,7 +102,10 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
     size_t pl = p->planes, mb = 0;
     for (int k = 0; k < 4; ++k) mb += up((size_t)L * pl * p->m_site[k] * 2);
     mb += up((size_t)(L + 1) * pl * p->m_env * 2);
-    mb += 2 * up(pl * p->m_t1 * 2) + 2 * up(pl * p->m_lp * 2) + 2 * up(pl * p->m_lpt * 2);
+    // the halves of the two-site environment: one of each, or one per site
+    // when they stay resident (keep_parts)
+    const size_t nparts = cfg->keep_parts ? (size_t)L : 1;
+    mb += 2 * up(pl * p->m_t1 * 2) + 2 * up(nparts * pl * p->m_lp * 2) + 2 * up(pl * p->m_lpt * 2);
     mb += up(pl * p->m_ct * 2) + up(p->m_part * 4) + ALIGN;
     mb += up(subspace_buffer_floats(p->cap) * 4) + 3 * ALIGN;
     mb += up(subspace_plane_elems_a(p->cap) * 2) + up(subspace_plane_elems_b(p->cap) * 2);
@@ -150,6 +153,9 @@ struct xtrg_ctx {
     std::vector<__nv_bfloat16*> env;
     __nv_bfloat16 *T1 = nullptr, *T1R = nullptr, *Lp = nullptr, *Rp = nullptr, *LpT = nullptr,
                   *RpT = nullptr, *Ct = nullptr;
+    // left half of site i / right half of site j (distinct buffers per site
+    // when keep_parts, else all alias Lp / Rp)
+    std::vector<__nv_bfloat16*> lpc, rpc;
     float* part = nullptr;
     int* err = nullptr;
     SubspaceBuffers sb{};
@@ -534,6 +540,7 @@ xtrg_status mixed_unit_env(xtrg_ctx* ctx, int slot) {
 
 // Lp from env[i] and site i (left half of Fig. VMPO(a), substeps 1-2)
 xtrg_status mixed_left_part(xtrg_ctx* ctx, const DevMpo& C, int i) {
+  __nv_bfloat16* Lp = ctx->m.lpc[i];
   const DevMpo& R = ctx->rho;
   const int P = ctx->m.P;
   const int a = R.dims[i], a2 = R.dims[i + 1], c = C.dims[i];
@@ -548,13 +555,14 @@ xtrg_status mixed_left_part(xtrg_ctx* ctx, const DevMpo& C, int i) {
   TcOperand At = opnd(ctx->m.T1, P, 2 * a2, 2 * a, ld1, 2LL * a2 * ld1, ctx->plan.m_t1, c);
   TcOperand Bp = opnd(ctx->m.site[1][i], P, 2 * a2, 2 * a, tc_ld(2 * a), 0, ctx->plan.m_site[1], 1);
   TRY(tc(ctx, At, Bp, 2 * a2, 2 * a2, 2 * a, c, 1,
-         out_planes(ctx->m.Lp, P, ctx->plan.m_lp, idx_split2(a2, 2 * ldL, 1),
+         out_planes(Lp, P, ctx->plan.m_lp, idx_split2(a2, 2 * ldL, 1),
                     idx_split2(a2, ldL, a2), 4 * ldL)));
   return XTRG_OK;
 }
 
 // Rp from env[j+1] and site j (right half)
 xtrg_status mixed_right_part(xtrg_ctx* ctx, const DevMpo& C, int j) {
+  __nv_bfloat16* Rp = ctx->m.rpc[j];
   const DevMpo& R = ctx->rho;
   const int P = ctx->m.P;
   const int a2 = R.dims[j], a3 = R.dims[j + 1], c2 = C.dims[j + 1];
@@ -569,7 +577,7 @@ xtrg_status mixed_right_part(xtrg_ctx* ctx, const DevMpo& C, int j) {
   TcOperand At = opnd(ctx->m.T1R, P, 2 * a2, 2 * a3, ld2, 2LL * a2 * ld2, ctx->plan.m_t1, c2);
   TcOperand Bq = opnd(ctx->m.site[3][j], P, 2 * a2, 2 * a3, tc_ld(2 * a3), 0, ctx->plan.m_site[3], 1);
   TRY(tc(ctx, At, Bq, 2 * a2, 2 * a2, 2 * a3, c2, 1,
-         out_planes(ctx->m.Rp, P, ctx->plan.m_lp, idx_split2(2, 1, 2LL * c2 * ldR),
+         out_planes(Rp, P, ctx->plan.m_lp, idx_split2(2, 1, 2LL * c2 * ldR),
                     idx_split2(2, a2, (long long)c2 * ldR), ldR)));
   return XTRG_OK;
 }
@@ -596,7 +604,8 @@ xtrg_status mixed_env(xtrg_ctx* ctx, const double* Csite, int kout, int kin, boo
 }
 
 // C_E = Lp Rp^T (FP32 accumulation, split-K partials summed in FP64)
-xtrg_status mixed_ce(xtrg_ctx* ctx, int m, int n, int a2) {
+xtrg_status mixed_ce(xtrg_ctx* ctx, const __nv_bfloat16* Lp, const __nv_bfloat16* Rp, int m, int n,
+                     int a2) {
   const int P = ctx->m.P;
   const long long K = (long long)a2 * a2, ld = tc_ld(K);
   const int kb = (int)((K + 63) / 64);
@@ -610,8 +619,8 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, int m, int n, int a2) {
   if (splitk > kb / 4) splitk = kb / 4;
   if (splitk < 1) splitk = 1;
   ctx->cur_tag = 3;
-  TcOperand Al = opnd(ctx->m.Lp, P, m, (int)K, ld, 0, ctx->plan.m_lp, 1);
-  TcOperand Br = opnd(ctx->m.Rp, P, n, (int)K, ld, 0, ctx->plan.m_lp, 1);
+  TcOperand Al = opnd(Lp, P, m, (int)K, ld, 0, ctx->plan.m_lp, 1);
+  TcOperand Br = opnd(Rp, P, n, (int)K, ld, 0, ctx->plan.m_lp, 1);
   TcOutput o;
   memset(&o, 0, sizeof o);
   o.mode = TC_OUT_PARTIAL; o.f32 = ctx->m.part; o.alpha = 1.0;
@@ -620,16 +629,46 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, int m, int n, int a2) {
   return XTRG_OK;
 }
 
+// One Newton-Schulz polar step Q <- Q (3I - Q^T Q)/2 in FP64 on the
+// orthonormal factor of a tensor-core split (orthonormal columns, or rows when
+// !columns).  The FP32 orthonormalisation leaves a defect d ~ 1e-7; the
+// variational update (Sec. II B) takes every site but the centre as an exact
+// isometry, so such defects bias each centre by ~d per site of the chain.
+// After the step the defect is O(d^2).  The centre factor is left as it is:
+// its own consistency error is ~d/2 and is recomputed by the next update.
+// Scratch: usbuf (k x k) and C_E (which the split has consumed).
+xtrg_status polish_isometry(xtrg_ctx* ctx, double* Q, int len, int k, bool columns) {
+  double* G = ctx->usbuf;
+  double* T = ctx->CE;
+  if (columns) {   // Q: len x k
+    TRY(gemm64(ctx, mk(k, k, len, 1, Q, idx_plain(1), idx_plain(k), 0, Q, idx_plain(k),
+                       idx_plain(1), 0, G, idx_plain(k), idx_plain(1), 0)));
+    CK(dev_polar_step(G, k, ctx->st));
+    TRY(gemm64(ctx, mk(len, k, k, 1, Q, idx_plain(k), idx_plain(1), 0, G, idx_plain(k),
+                       idx_plain(1), 0, T, idx_plain(k), idx_plain(1), 0)));
+  } else {         // Q: k x len
+    TRY(gemm64(ctx, mk(k, k, len, 1, Q, idx_plain(len), idx_plain(1), 0, Q, idx_plain(1),
+                       idx_plain(len), 0, G, idx_plain(k), idx_plain(1), 0)));
+    CK(dev_polar_step(G, k, ctx->st));
+    TRY(gemm64(ctx, mk(k, len, k, 1, G, idx_plain(k), idx_plain(1), 0, Q, idx_plain(len),
+                       idx_plain(1), 0, T, idx_plain(len), idx_plain(1), 0)));
+  }
+  CKM(cudaMemcpyAsync(Q, T, (size_t)len * k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  ctx->flops_split += 4.0 * len * (double)k * k;
+  return XTRG_OK;
+}
+
 xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
   const int L = ctx->L;
   const DevMpo& R = ctx->rho;
   const int kcap = dstar < ctx->cap ? dstar : ctx->cap;
+  const bool keep = ctx->cfg.keep_parts != 0;
   CKM(cudaMemsetAsync(ctx->m.err, 0, sizeof(int), ctx->st));
   TRY(mixed_unit_env(ctx, 0));
   TRY(mixed_unit_env(ctx, L));
   for (int j = L - 1; j >= 1; --j) {
     TRY(mixed_right_part(ctx, C, j));
-    TRY(mixed_env(ctx, C.site[j], C.dims[j], 4 * C.dims[j + 1], false, ctx->m.Rp, R.dims[j], j));
+    TRY(mixed_env(ctx, C.site[j], C.dims[j], 4 * C.dims[j + 1], false, ctx->m.rpc[j], R.dims[j], j));
   }
   double maxdisc = 0.0;
   for (int s = 0; s < sweeps; ++s) {
@@ -637,10 +676,14 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
     for (int dir = 0; dir < 2; ++dir) {
       for (int step = 0; step < L - 1; ++step) {
         const int i = dir == 0 ? step : L - 2 - step;
-        TRY(mixed_left_part(ctx, C, i));
-        TRY(mixed_right_part(ctx, C, i + 1));
+        // Left-to-right, the left half of bond i is new (environment i was
+        // just rebuilt) and the right half is unchanged since it was built
+        // from environment i+2; right-to-left the roles swap.  Resident
+        // halves are reused; otherwise both are rebuilt.
+        if (dir == 0 || !keep) TRY(mixed_left_part(ctx, C, i));
+        if (dir == 1 || !keep) TRY(mixed_right_part(ctx, C, i + 1));
         const int m = 4 * C.dims[i], n = 4 * C.dims[i + 2];
-        TRY(mixed_ce(ctx, m, n, R.dims[i + 1]));
+        TRY(mixed_ce(ctx, ctx->m.lpc[i], ctx->m.rpc[i + 1], m, n, R.dims[i + 1]));
         TRY(debug_check(ctx, "C_E", ctx->CE, (long long)m * n, i));
         // keep k = min(D*, m, n): the FP32-level C_E has no FP64-exact numerical rank
         int k = kcap < m ? kcap : m;
@@ -664,6 +707,10 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
           k = r.k;
           disc = r.discarded;
           ctx->fallbacks++;
+        } else if (dir == 0) {
+          TRY(polish_isometry(ctx, C.site[i], m, k, true));
+        } else {
+          TRY(polish_isometry(ctx, C.site[i + 1], n, k, false));
         }
         C.dims[i + 1] = k;
         TRY(debug_check(ctx, "left factor", C.site[i], (long long)m * k, i));
@@ -671,9 +718,9 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
         ctx->flops_split += 2.0 * m * (double)n * k * 2 + 3.0 * (2.0 * (dir == 0 ? m : n) * k * k);
         if (last && disc > maxdisc) maxdisc = disc;
         if (dir == 0)
-          TRY(mixed_env(ctx, C.site[i], k, m, true, ctx->m.Lp, R.dims[i + 1], i + 1));
+          TRY(mixed_env(ctx, C.site[i], k, m, true, ctx->m.lpc[i], R.dims[i + 1], i + 1));
         else
-          TRY(mixed_env(ctx, C.site[i + 1], k, n, false, ctx->m.Rp, R.dims[i + 1], i + 1));
+          TRY(mixed_env(ctx, C.site[i + 1], k, n, false, ctx->m.rpc[i + 1], R.dims[i + 1], i + 1));
         ctx->updates++;
       }
     }
@@ -831,8 +878,16 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
     for (int i = 0; ok && i <= L; ++i) ctx->m.env.push_back(eb + (size_t)i * P * p.m_env);
     ctx->m.T1 = (__nv_bfloat16*)carve(ctx, P * p.m_t1 * 2);
     ctx->m.T1R = (__nv_bfloat16*)carve(ctx, P * p.m_t1 * 2);
-    ctx->m.Lp = (__nv_bfloat16*)carve(ctx, P * p.m_lp * 2);
-    ctx->m.Rp = (__nv_bfloat16*)carve(ctx, P * p.m_lp * 2);
+    {
+      const size_t np = cfg->keep_parts ? (size_t)L : 1, one = (size_t)P * p.m_lp;
+      ctx->m.Lp = (__nv_bfloat16*)carve(ctx, np * one * 2);
+      ctx->m.Rp = (__nv_bfloat16*)carve(ctx, np * one * 2);
+      for (int i = 0; i < L && ctx->m.Lp && ctx->m.Rp; ++i) {
+        const size_t o = cfg->keep_parts ? (size_t)i * one : 0;
+        ctx->m.lpc.push_back(ctx->m.Lp + o);
+        ctx->m.rpc.push_back(ctx->m.Rp + o);
+      }
+    }
     ctx->m.LpT = (__nv_bfloat16*)carve(ctx, P * p.m_lpt * 2);
     ctx->m.RpT = (__nv_bfloat16*)carve(ctx, P * p.m_lpt * 2);
     ctx->m.Ct = (__nv_bfloat16*)carve(ctx, P * p.m_ct * 2);

@@ -16,14 +16,15 @@ class XTRG:
     returns the thermodynamics of Eq. ThermalQuan at the current beta."""
 
     def __init__(self, H_dims, H_sites, tau0, dstar, sweeps=4, order=4, init_sweeps=None,
-                 prec="fp64", beta_switch=0.0, svd_rel_tol=1e-15, device="cuda:0", stream=None):
+                 prec="fp64", beta_switch=0.0, svd_rel_tol=1e-15, device="cuda:0", stream=None,
+                 keep_parts=True):
         if not torch.cuda.is_available():
             raise RuntimeError("the XTRG engine needs a CUDA device")
         self.L = len(H_sites)
         self.device = torch.device(device)
         self._H = _lib.MpoArgs(H_dims, H_sites)
         self.cfg = _lib.make_config(tau0, order, dstar, sweeps, init_sweeps, prec, beta_switch,
-                                    svd_rel_tol)
+                                    svd_rel_tol, keep_parts)
         nbytes = _lib.xtrg_workspace_bytes(self._H, self.cfg)
         if nbytes == 0:
             raise _lib.XtrgError(_lib.XTRG_EINVAL, "bad Hamiltonian or configuration")

@@ -238,10 +238,12 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         for (int j = 0; j < j0; ++j) v = fmaf(-Ys[r][j], Ss[j * w + c], v);
         Ys[r][j0 + c] = v;
       }
-      // No barrier here: the next reduction writes a.red only after the
-      // next phase's first barrier, which every CTA reaches after its copy
-      // of a.red; and the partials are rewritten only after the barrier that
-      // ended this reduction.
+      // No grid barrier here: the next reduction writes a.red only after
+      // the next phase's first barrier, which every CTA reaches after its
+      // copy of a.red; and the partials are rewritten only after the barrier
+      // that ended this reduction.  The CTA barrier orders this CTA's row
+      // updates before the next phase reads them.
+      __syncthreads();
     }
     // ---- CholeskyQR2 inside the panel with an FP64 Gram and Cholesky;
     // columns whose pivot is at the FP64 noise floor carry no weight and are
@@ -288,7 +290,8 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         }
         for (int c = 0; c < w; ++c) Ys[r][j0 + c] = (float)x[c];
       }
-      // (no barrier: the same argument as for the projection passes)
+      // (no grid barrier: the same argument as for the projection passes)
+      __syncthreads();
     }
   }
   for (int e = tid; e < nr * k; e += ORTH_NT) {

@@ -39,7 +39,8 @@ struct SvdArgs {
   unsigned* bar;      // [0] arrivals, [1] generation
   int* rot;           // [3] rotations per sweep (ring)
   int* out;           // [0] k, [1] rank, [2] sweeps, [3] status (0 ok, 1 timeout, 2 not converged)
-  double* stats;      // [0] total weight, [1] discarded fraction, [2] sigma_max
+  double* stats;      // [0] total weight, [1] discarded fraction, [2] sigma_max,
+                      // [3] ||M||_F^2 (accumulated while loading)
 };
 
 // Grid barrier with a bounded wait.  Returns false if the wait expired or
@@ -93,16 +94,25 @@ __global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
 
   // load: column j of M (trans = 0) or of M^T (trans = 1); V = I
   const long long tot = (long long)a.len * a.ncols;
+  double ss = 0.0;
   for (long long e = gt; e < tot; e += GT) {
     int j = (int)(e / a.len), i = (int)(e % a.len);
-    a.W[e] = a.trans ? a.M[(long long)j * a.n + i] : a.M[(long long)i * a.n + j];
+    const double x = a.trans ? a.M[(long long)j * a.n + i] : a.M[(long long)i * a.n + j];
+    a.W[e] = x;
+    ss = fma(x, x, ss);
   }
+  ss = warp_sum(ss);
+  if (lane == 0) atomicAdd(a.stats + 3, ss);
   for (long long e = gt; e < (long long)a.ncols * a.ncols; e += GT) {
     int j = (int)(e / a.ncols), i = (int)(e % a.ncols);
     a.V[e] = (i == j) ? 1.0 : 0.0;
   }
   if (gt < 3) a.rot[gt] = 0;
   if (!grid_barrier(a)) return;
+  // Gram entries below eps^2 ||M||_F^2 are beneath the resolution of the
+  // whole problem: pairs of numerically-zero columns are not rotated (without
+  // this floor, columns of pure rounding noise can rotate without end)
+  const double gfloor = 4.930380657631324e-32 * ((volatile double*)a.stats)[3];
 
   const int mod = a.nn - 1;
   const int npairs = a.nn / 2;
@@ -130,7 +140,9 @@ __global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (!(fabs(ga) > a.tol * sqrt(al) * sqrt(be)) || al == 0.0 || be == 0.0) continue;
+        if (!(fabs(ga) > a.tol * sqrt(al) * sqrt(be)) || !(fabs(ga) > gfloor) || al == 0.0 ||
+            be == 0.0)
+          continue;
         // rotation zeroing the (p, q) Gram entry: t = sign(z)/(|z| + sqrt(1+z^2))
         double z = (be - al) / (2.0 * ga);
         double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + hypot(1.0, z));
@@ -263,6 +275,7 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
   a.stats = buf.stats;
   if ((e = cudaMemsetAsync(buf.counter, 0, 8 * sizeof(int), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(buf.kept, 0, 4 * sizeof(int), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(buf.stats, 0, 4 * sizeof(double), st)) != cudaSuccess) return e;
   int pairs = a.nn / 2;
   int grid = (pairs + WPB - 1) / WPB;
   long long work = (long long)len * ncols / (NT * 8);

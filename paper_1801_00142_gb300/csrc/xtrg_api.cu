@@ -852,7 +852,7 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   ctx->svd.V = (double*)carve(ctx, p.n_svd * 8);
   ctx->svd.sig = (double*)carve(ctx, p.n_svd_cols * 8);
   ctx->svd.perm = (int*)carve(ctx, p.n_svd_cols * 4);
-  ctx->svd.counter = (int*)carve(ctx, 16);
+  ctx->svd.counter = (int*)carve(ctx, 32);
   ctx->svd.kept = (int*)carve(ctx, 16);
   ctx->svd.stats = (double*)carve(ctx, 64);
   ctx->svd.max_elems = p.n_svd;

@@ -99,5 +99,3 @@ cudaError_t dev_fill(double* p, double v, long long n, cudaStream_t st);
 cudaError_t dev_scale(double* p, double v, long long n, cudaStream_t st);
 cudaError_t dev_sumsq(const double* p, long long n, double* out, cudaStream_t st);
 cudaError_t dev_identity_site(double* p, cudaStream_t st);
-// G <- (3I - G)/2 in place (k x k)
-cudaError_t dev_polar_step(double* G, int k, cudaStream_t st);

@@ -101,16 +101,6 @@ __global__ void sumsq_kernel(const double* __restrict__ p, long long n, double* 
   }
 }
 
-// G <- (3I - G)/2 for a k x k Gram matrix G (one Newton-Schulz polar step)
-__global__ void polar_step_kernel(double* G, int k) {
-  const long long n = (long long)k * k;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const bool diag = (e / k) == (e % k);
-    G[e] = (diag ? 3.0 : 0.0) * 0.5 - 0.5 * G[e];
-  }
-}
-
 __global__ void identity_site_kernel(double* p) {
   if (threadIdx.x < 4) p[threadIdx.x] = (threadIdx.x == 0 || threadIdx.x == 3) ? 1.0 : 0.0;
 }
@@ -152,12 +142,6 @@ cudaError_t dev_scale(double* p, double v, long long n, cudaStream_t st) {
 cudaError_t dev_sumsq(const double* p, long long n, double* out, cudaStream_t st) {
   note_launch();
   sumsq_kernel<<<1, 1024, 0, st>>>(p, n, out);
-  return cudaGetLastError();
-}
-
-cudaError_t dev_polar_step(double* G, int k, cudaStream_t st) {
-  note_launch();
-  polar_step_kernel<<<grid_for((long long)k * k), 256, 0, st>>>(G, k);
   return cudaGetLastError();
 }
 

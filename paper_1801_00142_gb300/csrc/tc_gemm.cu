@@ -149,6 +149,78 @@ __device__ __forceinline__ void store_out(const TcOutput& o, long long off, floa
   }
 }
 
+__device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 x) {
+  return (uint32_t)__bfloat16_as_ushort(x);
+}
+
+// Split two values into up to three BF16 planes and pack each plane's pair
+// (first value in the low half: the lower address).
+__device__ __forceinline__ void split_pack2(float a, float b, uint32_t& w0, uint32_t& w1,
+                                            uint32_t& w2) {
+  const __nv_bfloat16 a0 = __float2bfloat16_rn(a), b0 = __float2bfloat16_rn(b);
+  const float ar = a - __bfloat162float(a0), br = b - __bfloat162float(b0);
+  const __nv_bfloat16 a1 = __float2bfloat16_rn(ar), b1 = __float2bfloat16_rn(br);
+  const __nv_bfloat16 a2 = __float2bfloat16_rn(ar - __bfloat162float(a1));
+  const __nv_bfloat16 b2 = __float2bfloat16_rn(br - __bfloat162float(b1));
+  w0 = bf16_bits(a0) | (bf16_bits(b0) << 16);
+  w1 = bf16_bits(a1) | (bf16_bits(b1) << 16);
+  w2 = bf16_bits(a2) | (bf16_bits(b2) << 16);
+}
+
+// Store 32 consecutive output columns of one row (v[0..31] already scaled).
+// Column layout of the chunk, decided once per tile: contiguous (32 columns
+// at consecutive offsets), paired (columns 2j, 2j+1 adjacent) or scattered.
+// Vector stores need the lane's start offset aligned (8 elements for BF16
+// planes / 4 for FP32) and the plane stride likewise; otherwise narrower
+// stores are used.
+__device__ __forceinline__ void store_chunk(const TcOutput& o, long long om,
+                                            const long long* col, int layout, int ncols,
+                                            const float* v) {
+  if (o.mode == TC_OUT_BF16P) {
+    const long long ps = o.plane_stride;
+    const long long off0 = om + col[0];
+    if (layout == 2 && ncols == 32 && ((off0 | ps) & 7) == 0) {
+#pragma unroll
+      for (int q8 = 0; q8 < 4; ++q8) {
+        uint32_t w[3][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          split_pack2(v[q8 * 8 + 2 * e], v[q8 * 8 + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
+        __nv_bfloat16* d = o.bf16 + off0 + q8 * 8;
+        *reinterpret_cast<uint4*>(d) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+        *reinterpret_cast<uint4*>(d + ps) = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+        if (o.planes > 2)
+          *reinterpret_cast<uint4*>(d + 2 * ps) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+      }
+      return;
+    }
+    if (layout >= 1 && ncols == 32 && ((om + col[0]) & 1) == 0 && (ps & 1) == 0) {
+#pragma unroll
+      for (int jj = 0; jj < 32; jj += 2) {
+        const long long off = om + col[jj];
+        uint32_t w0, w1, w2;
+        split_pack2(v[jj], v[jj + 1], w0, w1, w2);
+        *reinterpret_cast<uint32_t*>(o.bf16 + off) = w0;
+        *reinterpret_cast<uint32_t*>(o.bf16 + off + ps) = w1;
+        if (o.planes > 2) *reinterpret_cast<uint32_t*>(o.bf16 + off + 2 * ps) = w2;
+      }
+      return;
+    }
+  } else {
+    const long long off0 = om + col[0];
+    if (layout == 2 && ncols == 32 && (off0 & 3) == 0) {
+      float4* d = reinterpret_cast<float4*>(o.f32 + off0);
+#pragma unroll
+      for (int q4 = 0; q4 < 8; ++q4)
+        d[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj)
+    if (jj < ncols) store_out(o, om + col[jj], v[jj]);
+}
+
 // Persistent kernel: every CTA walks the output tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ... (tile order: n fastest, then m, then batch x
 // split).  The accumulator is double-buffered in tensor memory (2 x 128
@@ -284,6 +356,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         col_off[cc] = (o.mode == TC_OUT_PARTIAL || n >= p.N) ? (long long)n : idx_off(o.cn, n);
       }
       __syncwarp();
+      // layout of each 32-column chunk (2 bits per chunk: 2 contiguous, 1 paired)
+      int layouts = 0;
+#pragma unroll
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        const long long mine = col_off[ch * 32 + lane];
+        const bool contig = mine == col_off[ch * 32] + lane;
+        // paired: every even column's partner follows it, and all pair starts
+        // have the parity of the chunk's first column (one alignment test
+        // per row then covers the whole chunk)
+        const bool paired = (lane & 1) || (col_off[ch * 32 + lane + 1] == mine + 1 &&
+                                           ((mine - col_off[ch * 32]) & 1) == 0);
+        const unsigned mc = __ballot_sync(0xffffffffu, contig);
+        const unsigned mp = __ballot_sync(0xffffffffu, paired);
+        layouts |= (mc == 0xffffffffu ? 2 : (mp == 0xffffffffu ? 1 : 0)) << (2 * ch);
+      }
       if (!mbar_wait(&acc_full[buf], (uint32_t)((j >> 1) & 1), p.err)) break;
       fence_after();
       const int m = m0 + q * 32 + lane;
@@ -312,14 +399,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                          : "memory");
         }
         if (!row_ok) continue;
+        const int ncols = min(32, p.N - (n0 + c));
+        if (ncols <= 0) continue;
         if (o.mode == TC_OUT_PARTIAL) {
+          float* d = dstp + n0 + c;
+          if (ncols == 32 && ((uintptr_t)d & 15) == 0) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            if (n0 + c + jj < p.N) dstp[n0 + c + jj] = v[jj];
+            for (int q4 = 0; q4 < 8; ++q4)
+              reinterpret_cast<float4*>(d)[q4] =
+                  make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj)
+              if (jj < ncols) d[jj] = v[jj];
+          }
         } else {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            if (n0 + c + jj < p.N) store_out(o, om + col_off[c + jj], alpha * v[jj]);
+          for (int jj = 0; jj < 32; ++jj) v[jj] *= alpha;
+          store_chunk(o, om, col_off + c, (layouts >> (2 * (c / 32))) & 3, ncols, v);
         }
       }
     }

@@ -439,7 +439,7 @@ bool mixed_for_beta(const xtrg_ctx* ctx, double beta) {
 // ============================================================ tensor-core path
 // The doubling product A = B = rho with every contraction on tcgen05.  Layouts
 // (all operands K-major, BF16 planes, rows padded to tc_ld):
-//   site copies  sT[(t,s,a')][a]   sP[(u,b')][(b,t)]   sN[(a',t',s')][a'']   sQ[(b',u')][(t',b'')]
+//   site copies  sT[(s,a',t)][a]   sP[(u,b')][(b,t)]   sN[(a',t',s')][a'']   sQ[(b',u')][(t',b'')]
 //   environment  V[c][b][a]                 (left and right alike)
 //   left half    T1[c][(s,a')][(b,t)]  ->  Lp[(c,s,u)][(b',a')]
 //   right half   T1R[c''][(a',s')][(t',b'')]  ->  Rp[(s',u',c'')][(b',a')]
@@ -518,8 +518,11 @@ xtrg_status mixed_prepare(xtrg_ctx* ctx) {
   for (int i = 0; i < ctx->L; ++i) {
     const int l = R.dims[i], r = R.dims[i + 1];
     const double* w = R.site[i];
-    CKM(to_planes(w, idx_plain(1), idx_plain(4LL * r), 0, 4 * r, l, 1, ctx->m.site[0][i],
-                  tc_ld(l), 0, P, ctx->plan.m_site[0], ctx->st));
+    // rows (s, a', t): t, which pairs with b in T1's contraction index
+    // (b, t), is innermost, so the epilogue writes each (b, t) pair as one
+    // 4-byte store per plane
+    CKM(to_planes(w, idx_split3(r, 2, r, 1, 2LL * r), idx_plain(4LL * r), 0, 4 * r, l, 1,
+                  ctx->m.site[0][i], tc_ld(l), 0, P, ctx->plan.m_site[0], ctx->st));
     CKM(to_planes(w, idx_plain(1), idx_plain(2LL * r), 0, 2 * r, 2 * l, 1, ctx->m.site[1][i],
                   tc_ld(2 * l), 0, P, ctx->plan.m_site[1], ctx->st));
     CKM(to_planes(w, idx_plain(r), idx_plain(1), 0, 4 * l, r, 1, ctx->m.site[2][i], tc_ld(r), 0, P,
@@ -550,7 +553,7 @@ xtrg_status mixed_left_part(xtrg_ctx* ctx, const DevMpo& C, int i) {
   TcOperand Bs = opnd(ctx->m.site[0][i], P, 4 * a2, a, tc_ld(a), 0, ctx->plan.m_site[0], 1);
   TRY(tc(ctx, Ae, Bs, a, 4 * a2, a, c, 1,
          out_planes(ctx->m.T1, P, ctx->plan.m_t1, idx_plain(2),
-                    idx_split3(2, a2, 1, (long long)a2 * ld1, ld1), 2LL * a2 * ld1)));
+                    idx_split3(a2, 2, (long long)a2 * ld1, ld1, 1), 2LL * a2 * ld1)));
   ctx->cur_tag = 2;
   TcOperand At = opnd(ctx->m.T1, P, 2 * a2, 2 * a, ld1, 2LL * a2 * ld1, ctx->plan.m_t1, c);
   TcOperand Bp = opnd(ctx->m.site[1][i], P, 2 * a2, 2 * a, tc_ld(2 * a), 0, ctx->plan.m_site[1], 1);
@@ -629,35 +632,6 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, const __nv_bfloat16* Lp, const __nv_bfloat16
   return XTRG_OK;
 }
 
-// One Newton-Schulz polar step Q <- Q (3I - Q^T Q)/2 in FP64 on the
-// orthonormal factor of a tensor-core split (orthonormal columns, or rows when
-// !columns).  The FP32 orthonormalisation leaves a defect d ~ 1e-7; the
-// variational update (Sec. II B) takes every site but the centre as an exact
-// isometry, so such defects bias each centre by ~d per site of the chain.
-// After the step the defect is O(d^2).  The centre factor is left as it is:
-// its own consistency error is ~d/2 and is recomputed by the next update.
-// Scratch: usbuf (k x k) and C_E (which the split has consumed).
-xtrg_status polish_isometry(xtrg_ctx* ctx, double* Q, int len, int k, bool columns) {
-  double* G = ctx->usbuf;
-  double* T = ctx->CE;
-  if (columns) {   // Q: len x k
-    TRY(gemm64(ctx, mk(k, k, len, 1, Q, idx_plain(1), idx_plain(k), 0, Q, idx_plain(k),
-                       idx_plain(1), 0, G, idx_plain(k), idx_plain(1), 0)));
-    CK(dev_polar_step(G, k, ctx->st));
-    TRY(gemm64(ctx, mk(len, k, k, 1, Q, idx_plain(k), idx_plain(1), 0, G, idx_plain(k),
-                       idx_plain(1), 0, T, idx_plain(k), idx_plain(1), 0)));
-  } else {         // Q: k x len
-    TRY(gemm64(ctx, mk(k, k, len, 1, Q, idx_plain(len), idx_plain(1), 0, Q, idx_plain(1),
-                       idx_plain(len), 0, G, idx_plain(k), idx_plain(1), 0)));
-    CK(dev_polar_step(G, k, ctx->st));
-    TRY(gemm64(ctx, mk(k, len, k, 1, G, idx_plain(k), idx_plain(1), 0, Q, idx_plain(len),
-                       idx_plain(1), 0, T, idx_plain(len), idx_plain(1), 0)));
-  }
-  CKM(cudaMemcpyAsync(Q, T, (size_t)len * k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-  ctx->flops_split += 4.0 * len * (double)k * k;
-  return XTRG_OK;
-}
-
 xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
   const int L = ctx->L;
   const DevMpo& R = ctx->rho;
@@ -707,10 +681,6 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
           k = r.k;
           disc = r.discarded;
           ctx->fallbacks++;
-        } else if (dir == 0) {
-          TRY(polish_isometry(ctx, C.site[i], m, k, true));
-        } else {
-          TRY(polish_isometry(ctx, C.site[i + 1], n, k, false));
         }
         C.dims[i + 1] = k;
         TRY(debug_check(ctx, "left factor", C.site[i], (long long)m * k, i));

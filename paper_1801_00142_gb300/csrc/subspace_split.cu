@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
   __shared__ float Ys[ROWS_PER_CTA][MAX_K + 1];
   __shared__ __align__(16) float Ss[MAX_K * PANEL];
   __shared__ double Ld[PANEL][PANEL + 1];
+  __shared__ double Linv[PANEL];   // reciprocals of the Cholesky pivots (0 for dead columns)
   const int tid = threadIdx.x;
   const int r0 = blockIdx.x * ROWS_PER_CTA;
   const int nr = min(ROWS_PER_CTA, a.rows - r0);
@@ -269,10 +270,15 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         for (int j = 0; j < w; ++j) {
           const double pj = Ld[j][j];
           const bool dead = !(pj > thr) || !(dmax > 0.0);
-          const double d = dead ? 0.0 : sqrt(pj);
+          // one FP64 square root and reciprocal per pivot (lane j), then
+          // multiplications: FP64 division is a long instruction sequence
+          if (lane == j) {
+            const double d = dead ? 0.0 : sqrt(pj);
+            Ld[j][j] = d;
+            Linv[j] = dead ? 0.0 : 1.0 / d;
+          }
           __syncwarp();
-          if (lane == j) Ld[j][j] = d;
-          if (lane > j && lane < w) Ld[lane][j] = dead ? 0.0 : Ld[lane][j] / d;
+          if (lane > j && lane < w) Ld[lane][j] = Ld[lane][j] * Linv[j];
           __syncwarp();
           if (lane > j && lane < w)
             for (int c = j + 1; c <= lane; ++c) Ld[lane][c] -= Ld[lane][j] * Ld[c][j];
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
         for (int c = 0; c < w; ++c) {
           double v = (double)Ys[r][j0 + c];
           for (int d = 0; d < c; ++d) v = fma(-x[d], Ld[c][d], v);
-          x[c] = Ld[c][c] > 0.0 ? v / Ld[c][c] : 0.0;
+          x[c] = v * Linv[c];
         }
         for (int c = 0; c < w; ++c) Ys[r][j0 + c] = (float)x[c];
       }

@@ -14,15 +14,19 @@
 //
 // orth() is block classical Gram-Schmidt over panels of 32 columns: two FP32
 // projection passes against the earlier panels, then CholeskyQR2 inside the
-// panel with the 32 x 32 Gram and its Cholesky factor in FP64.  Columns whose
+// panel with the 32 x 32 Gram and its Cholesky factor in FP64 (or, in the
+// cluster kernel below, a double-float Gram and FP64 Cholesky).  Columns whose
 // Cholesky pivot sits at the FP64 noise floor carry no weight and are set to
-// zero instead of being divided by that pivot.  It runs as one persistent
-// cooperative kernel: every CTA keeps its slab of rows in shared memory,
-// reductions over rows go through per-CTA partials in global memory (summed
-// in a fixed order, so results are deterministic), and phases are separated
-// by bounded grid barriers.  The caller checks max |U^T U - I| over the live
+// zero instead of being divided by that pivot.  Up to 16 x 64 rows it runs in
+// one thread-block cluster (orth_cluster); beyond that, or where such a
+// cluster cannot be resident, as one persistent cooperative kernel: every
+// CTA keeps its slab of rows in shared memory, reductions over rows go
+// through per-CTA partials in global memory (summed in a fixed order, so
+// results are deterministic), and phases are separated by bounded grid
+// barriers.  The caller checks max |U^T U - I| over the live
 // columns and takes the exact split when the FP32 projections lost
 // orthogonality (steep, rank-deficient spectra).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -306,6 +310,258 @@ __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// The same block Gram-Schmidt inside one thread-block cluster of OC_NC CTAs
+// (rows <= OC_NC * OC_RMAX).  Each CTA keeps its slab of rows in shared
+// memory; every reduction over rows is a reduce-scatter and an all-gather
+// through distributed shared memory between two cluster barriers, instead
+// of two grid-wide barriers and a pass through L2.  The in-panel work is
+// spread over the CTA: the panel Gram is accumulated in double-float FP32
+// (exact products, compensated sums: FP32 pipes, about 44 significant bits),
+// the 32 x 32 Cholesky runs right-looking on all threads in FP64, and the
+// triangular solve is a product with L^{-1} (FP64, split into two floats)
+// in double-float arithmetic.  Dead columns are handled as in the grid
+// kernel.  Every CTA runs the same sequence of cluster barriers (no early
+// exit), and a last barrier keeps each CTA's shared memory alive until its
+// peers have read it.
+namespace cg = cooperative_groups;
+
+constexpr int OC_NC = 16;
+constexpr int OC_RMAX = 64;
+constexpr int OC_NT = 256;
+constexpr int OC_BUF = MAX_K * PANEL;           // floats per exchange buffer
+constexpr int OC_OUT = OC_RMAX * PANEL / OC_NT;  // panel outputs per thread
+
+struct OrthClusterArgs {
+  float* Y;
+  int rows, k, rpc;   // rpc: rows per CTA (<= OC_RMAX)
+};
+
+// s + e = a + b exactly (round-to-nearest adds, never contracted)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += a * b with the product exact (fma residual)
+__device__ __forceinline__ void df_fma(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  float t, e;
+  two_sum(hi, p, t, e);
+  hi = t;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+size_t orth_cluster_smem(int k) {
+  return (size_t)OC_RMAX * (k + 1) * 4      // Ys
+         + 3 * (size_t)OC_BUF * 4           // Pf, Rf, Ss
+         + 3 * (size_t)PANEL * (PANEL + 1) * 8   // Ld, Lf, Li
+         + 2 * (size_t)PANEL * (PANEL + 1) * 4   // Lh, Ll
+         + PANEL * 8 + 64;                  // Linv, alignment slack
+}
+
+__global__ void __launch_bounds__(OC_NT, 1) orth_cluster(OrthClusterArgs a) {
+  extern __shared__ __align__(16) unsigned char oc_smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x;
+  const int rank = (int)cluster.block_rank();
+  const int k = a.k, ld = k + 1;
+  double* Ld = reinterpret_cast<double*>(oc_smem);              // working Gram [PANEL][PANEL+1]
+  double* Lf = Ld + PANEL * (PANEL + 1);                        // Cholesky factor
+  double* Li = Lf + PANEL * (PANEL + 1);                        // its inverse
+  double* Linv = Li + PANEL * (PANEL + 1);                      // reciprocal pivots
+  float* Pf = reinterpret_cast<float*>(Linv + PANEL);           // partials (peers read)
+  float* Rf = Pf + OC_BUF;                                      // owned sums (peers read)
+  float* Ss = Rf + OC_BUF;                                      // gathered coefficients
+  float* Lh = Ss + OC_BUF;                                      // L^{-1} high part
+  float* Ll = Lh + PANEL * (PANEL + 1);                         // L^{-1} low part
+  float* Ys = Ll + PANEL * (PANEL + 1);                         // rows x ld
+  double* Pd = reinterpret_cast<double*>(Pf);
+  double* Rd = reinterpret_cast<double*>(Rf);
+  const int r0 = rank * a.rpc;
+  const int nr = max(0, min(a.rpc, a.rows - r0));
+  for (int e = tid; e < OC_RMAX * ld; e += OC_NT) {
+    const int r = e / ld, c = e % ld;
+    Ys[e] = (r < nr && c < k) ? a.Y[(long long)(r0 + r) * k + c] : 0.f;
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < k; j0 += PANEL) {
+    const int w = min(PANEL, k - j0);
+    // ---- two projection passes against columns [0, j0)
+    for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
+      const int n = j0 * w;
+      for (int e = tid; e < n; e += OC_NT) {
+        const int j = e / w, c = e % w;
+        float sacc = 0.f;
+        for (int r = 0; r < nr; ++r) sacc = fmaf(Ys[r * ld + j], Ys[r * ld + j0 + c], sacc);
+        Pf[e] = sacc;
+      }
+      cluster.sync();
+      const int sl = (n + OC_NC - 1) / OC_NC;
+      const int lo = rank * sl, hi = min(n, lo + sl);
+      for (int e = lo + tid; e < hi; e += OC_NT) {
+        float sacc = 0.f;
+        for (int q = 0; q < OC_NC; ++q) sacc += cluster.map_shared_rank(Pf, q)[e];
+        Rf[e] = sacc;
+      }
+      cluster.sync();
+      for (int e = tid; e < n; e += OC_NT) Ss[e] = cluster.map_shared_rank(Rf, e / sl)[e];
+      __syncthreads();
+      for (int e = tid; e < nr * w; e += OC_NT) {
+        const int r = e / w, c = e % w;
+        float v = Ys[r * ld + j0 + c];
+        for (int j = 0; j < j0; ++j) v = fmaf(-Ys[r * ld + j], Ss[j * w + c], v);
+        Ys[r * ld + j0 + c] = v;
+      }
+      __syncthreads();
+    }
+    // ---- CholeskyQR2 inside the panel
+    for (int pass = 0; pass < 2; ++pass) {
+      const int n2 = w * w;
+      for (int e = tid; e < n2; e += OC_NT) {
+        const int c = e / w, d = e % w;
+        float h = 0.f, l = 0.f;
+        for (int r = 0; r < nr; ++r) df_fma(Ys[r * ld + j0 + c], Ys[r * ld + j0 + d], h, l);
+        Pd[e] = (double)h + (double)l;
+      }
+      cluster.sync();
+      const int sl = (n2 + OC_NC - 1) / OC_NC;
+      const int lo = rank * sl, hi = min(n2, lo + sl);
+      for (int e = lo + tid; e < hi; e += OC_NT) {
+        double sacc = 0.0;
+        for (int q = 0; q < OC_NC; ++q) sacc += cluster.map_shared_rank(Pd, q)[e];
+        Rd[e] = sacc;
+      }
+      cluster.sync();
+      for (int e = tid; e < n2; e += OC_NT)
+        Ld[(e / w) * (PANEL + 1) + e % w] = cluster.map_shared_rank(Rd, e / sl)[e];
+      for (int e = tid; e < PANEL * (PANEL + 1); e += OC_NT) {
+        Lf[e] = 0.0;
+        Li[e] = 0.0;
+      }
+      __syncthreads();
+      double dmax = 0.0;
+      for (int c = 0; c < w; ++c) dmax = fmax(dmax, Ld[c * (PANEL + 1) + c]);
+      const double thr = 1e-13 * dmax;
+      // right-looking Cholesky: the working Gram's column j stays unscaled
+      // during step j, the factor goes to Lf (no read/write overlap)
+      for (int j = 0; j < w; ++j) {
+        if (tid == 0) {
+          const double pj = Ld[j * (PANEL + 1) + j];
+          const bool dead = !(pj > thr) || !(dmax > 0.0);
+          const double dg = dead ? 0.0 : sqrt(pj);
+          Lf[j * (PANEL + 1) + j] = dg;
+          Linv[j] = dead ? 0.0 : 1.0 / dg;
+        }
+        __syncthreads();
+        const double lj = Linv[j];
+        const int t = w - 1 - j;
+        for (int i = j + 1 + tid; i < w; i += OC_NT) Lf[i * (PANEL + 1) + j] = Ld[i * (PANEL + 1) + j] * lj;
+        const double lj2 = lj * lj;
+        for (int e = tid; e < t * t; e += OC_NT) {
+          const int ii = j + 1 + e / t, cc = j + 1 + e % t;
+          if (cc <= ii)
+            Ld[ii * (PANEL + 1) + cc] -= Ld[ii * (PANEL + 1) + j] * Ld[cc * (PANEL + 1) + j] * lj2;
+        }
+        __syncthreads();
+      }
+      // L^{-1}: lane i builds column i by forward substitution
+      if (tid < w) {
+        const int i = tid;
+        Li[i * (PANEL + 1) + i] = Linv[i];
+        for (int j = i + 1; j < w; ++j) {
+          double sacc = 0.0;
+          for (int m = i; m < j; ++m) sacc = fma(Lf[j * (PANEL + 1) + m], Li[m * (PANEL + 1) + i], sacc);
+          Li[j * (PANEL + 1) + i] = -Linv[j] * sacc;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < n2; e += OC_NT) {
+        const int c = e / w, d = e % w;
+        const double x = Li[c * (PANEL + 1) + d];
+        const float xh = (float)x;
+        Lh[c * (PANEL + 1) + d] = xh;
+        Ll[c * (PANEL + 1) + d] = (float)(x - (double)xh);
+      }
+      __syncthreads();
+      // rows <- rows L^{-T}: x[r][c] = sum_{d <= c} L^{-1}[c][d] y[r][d]
+      float outv[OC_OUT];
+#pragma unroll
+      for (int t = 0; t < OC_OUT; ++t) {
+        const int e = tid + t * OC_NT;
+        float h = 0.f, l = 0.f;
+        if (e < nr * w) {
+          const int r = e / w, c = e % w;
+          for (int d = 0; d <= c; ++d) {
+            const float y = Ys[r * ld + j0 + d];
+            df_fma(y, Lh[c * (PANEL + 1) + d], h, l);
+            l = __fmaf_rn(y, Ll[c * (PANEL + 1) + d], l);
+          }
+        }
+        outv[t] = h + l;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < OC_OUT; ++t) {
+        const int e = tid + t * OC_NT;
+        if (e < nr * w) Ys[(e / w) * ld + j0 + e % w] = outv[t];
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < nr * k; e += OC_NT) {
+    const int r = e / k, c = e % k;
+    a.Y[(long long)(r0 + r) * k + c] = Ys[r * ld + c];
+  }
+  // peers may still be reading this CTA's exchange buffers
+  cluster.sync();
+}
+
+int g_orth_cluster_state = 0;   // 0 unknown, 1 available, -1 unavailable
+
+// Launch configuration of orth_cluster (one cluster of OC_NC CTAs).
+cudaLaunchConfig_t orth_cluster_config(size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(OC_NC);
+  cfg.blockDim = dim3(OC_NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = OC_NC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Whether one cluster of OC_NC CTAs with the largest shared-memory request
+// can be resident on this device (asked once; no kernel runs for it).
+bool orth_cluster_available() {
+  if (g_orth_cluster_state != 0) return g_orth_cluster_state > 0;
+  g_orth_cluster_state = -1;
+  const size_t smem = orth_cluster_smem(MAX_K);
+  if (cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = orth_cluster_config(smem, 0, attr);
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, orth_cluster, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (nclusters >= 1) g_orth_cluster_state = 1;
+  return g_orth_cluster_state > 0;
+}
+
 int g_orth_max_ctas = 0;
 
 GemmF32 g32(int M, int N, int K, const float* A, Idx3 am, Idx3 ak, const float* B, Idx3 bk,
@@ -330,6 +586,18 @@ cudaError_t orth_check(const float* Q, int rows, int k, const SubspaceBuffers& b
 
 cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
   if (k > MAX_K) return cudaErrorInvalidValue;
+  if (rows <= OC_NC * OC_RMAX && orth_cluster_available()) {
+    OrthClusterArgs ca;
+    ca.Y = Y; ca.rows = rows; ca.k = k;
+    ca.rpc = (rows + OC_NC - 1) / OC_NC;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = orth_cluster_config(orth_cluster_smem(k), st, attr);
+    note_launch();
+    if (cudaLaunchKernelEx(&cfg, orth_cluster, ca) == cudaSuccess) return cudaSuccess;
+    // the cluster could not be launched: use the grid-wide kernel from now on
+    cudaGetLastError();
+    g_orth_cluster_state = -1;
+  }
   const int G = (rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
   if (g_orth_max_ctas == 0) {
     int dev = 0, sms = 0, per = 0;

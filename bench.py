@@ -295,6 +295,8 @@ def run_native(args):
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": s1["kernel_launches"] - s0["kernel_launches"],
            "exact_split_fallbacks": s1["exact_split_fallbacks"] - s0["exact_split_fallbacks"],
+           "truncation_ms_per_step": (s1["split_ms"] - s0["split_ms"]) / args.steps,
+           "orth_cluster_calls": s1["orth_cluster_calls"] - s0["orth_cluster_calls"],
            "observables_last": {k: rows[-1][k] for k in ("beta", "lnZ", "f", "u", "max_bond")}}
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(2)

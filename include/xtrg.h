@@ -149,6 +149,8 @@ typedef struct {
   long long tc_launches;     /* tensor-core GEMM launches (only while profiling)     */
   long long kernel_launches; /* kernels launched by this library, all contexts      */
   long long exact_split_fallbacks; /* tensor-core-path updates that took the exact FP64 split */
+  double split_ms;           /* device time of the tensor-core truncations (only while profiling) */
+  long long orth_cluster_calls; /* orthonormalisations run as one thread-block cluster, all contexts */
 } xtrg_stats;
 
 /* Counters since creation (kernel_launches: since the library was loaded). */

@@ -54,7 +54,8 @@ class xtrg_stats(C.Structure):
     _fields_ = [("contraction_flops", C.c_double), ("split_flops", C.c_double),
                 ("tc_flops", C.c_double), ("tc_ms", C.c_double),
                 ("two_site_updates", C.c_longlong), ("tc_launches", C.c_longlong),
-                ("kernel_launches", C.c_longlong), ("exact_split_fallbacks", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("exact_split_fallbacks", C.c_longlong),
+                ("split_ms", C.c_double), ("orth_cluster_calls", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

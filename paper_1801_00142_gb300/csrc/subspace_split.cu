@@ -593,7 +593,10 @@ cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaS
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = orth_cluster_config(orth_cluster_smem(k), st, attr);
     note_launch();
-    if (cudaLaunchKernelEx(&cfg, orth_cluster, ca) == cudaSuccess) return cudaSuccess;
+    if (cudaLaunchKernelEx(&cfg, orth_cluster, ca) == cudaSuccess) {
+      __atomic_add_fetch(&g_orth_cluster_calls, 1ull, __ATOMIC_RELAXED);
+      return cudaSuccess;
+    }
     // the cluster could not be launched: use the grid-wide kernel from now on
     cudaGetLastError();
     g_orth_cluster_state = -1;
@@ -620,6 +623,8 @@ cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaS
 }
 
 }  // namespace
+
+unsigned long long g_orth_cluster_calls = 0;
 
 size_t subspace_plane_elems_a(int cap) { return 3 * (size_t)(4 * cap) * tc_ld(4 * cap); }
 size_t subspace_plane_elems_b(int cap) { return 3 * (size_t)(4 * cap) * tc_ld(4 * cap); }

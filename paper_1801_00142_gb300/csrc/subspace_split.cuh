@@ -22,6 +22,9 @@ struct SubspaceBuffers {
   int* err;            // bounded-wait error flag of the tensor-core GEMM
 };
 
+// Orthonormalisations launched as one thread-block cluster (all contexts).
+extern unsigned long long g_orth_cluster_calls;
+
 // BF16 elements of pa and pb for bond capacity cap.
 size_t subspace_plane_elems_a(int cap);
 size_t subspace_plane_elems_b(int cap);

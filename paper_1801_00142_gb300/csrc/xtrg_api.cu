@@ -173,7 +173,7 @@ struct xtrg_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
-  double tc_flops = 0.0, tc_ms = 0.0;
+  double tc_flops = 0.0, tc_ms = 0.0, split_ms = 0.0;
   long long tc_launches = 0;
   std::vector<int> ev_tag;             // call site of each event pair
   double tag_ms[8] = {0}, tag_flops[8] = {0};
@@ -469,6 +469,26 @@ TcOutput out_planes(__nv_bfloat16* base, int P, long long ps, Idx3 cm, Idx3 cn, 
                   cudaGetErrorString(_e));                                                  \
   } while (0)
 
+// Profiling: a pair of events around a stretch of stream work, tagged with
+// its call site (tags 0-4: tensor-core GEMMs, 5: truncation); the first is
+// recorded here, the second by the caller after the work.
+constexpr int TAG_SPLIT = 5;
+xtrg_status ev_pair(xtrg_ctx* ctx, int tag, cudaEvent_t* e0, cudaEvent_t* e1) {
+  if (ctx->ev_used + 2 > ctx->ev.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      CKM(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+  }
+  *e0 = ctx->ev[ctx->ev_used++];
+  *e1 = ctx->ev[ctx->ev_used++];
+  ctx->ev_tag.push_back(tag);
+  ctx->tag_n[tag]++;
+  CKM(cudaEventRecord(*e0, ctx->st));
+  return XTRG_OK;
+}
+
 xtrg_status tc(xtrg_ctx* ctx, const TcOperand& A, const TcOperand& B, int M, int N, int K,
                int batch, int splitk, const TcOutput& o) {
   const double fl = 2.0 * M * (double)N * K * batch;
@@ -476,19 +496,8 @@ xtrg_status tc(xtrg_ctx* ctx, const TcOperand& A, const TcOperand& B, int M, int
   ctx->tc_flops += fl;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->profiling) {
-    if (ctx->ev_used + 2 > ctx->ev.size()) {
-      for (int i = 0; i < 256; ++i) {
-        cudaEvent_t e;
-        CKM(cudaEventCreate(&e));
-        ctx->ev.push_back(e);
-      }
-    }
-    e0 = ctx->ev[ctx->ev_used++];
-    e1 = ctx->ev[ctx->ev_used++];
-    ctx->ev_tag.push_back(ctx->cur_tag);
+    TRY(ev_pair(ctx, ctx->cur_tag, &e0, &e1));
     ctx->tag_flops[ctx->cur_tag] += fl;
-    ctx->tag_n[ctx->cur_tag]++;
-    CKM(cudaEventRecord(e0, ctx->st));
   }
   CKM(tc_gemm(A, B, M, N, K, batch, ctx->m.nprod, splitk, o, ctx->m.err, ctx->st));
   if (e1) {
@@ -502,9 +511,17 @@ xtrg_status tc(xtrg_ctx* ctx, const TcOperand& A, const TcOperand& B, int M, int
 xtrg_status resolve_events(xtrg_ctx* ctx) {
   for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
     float ms = 0.f;
-    CKM(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
-    ctx->tc_ms += ms;
-    if (i / 2 < ctx->ev_tag.size()) ctx->tag_ms[ctx->ev_tag[i / 2]] += ms;
+    // a pair left open by a call that failed midway is skipped
+    if (cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const int tag = i / 2 < ctx->ev_tag.size() ? ctx->ev_tag[i / 2] : 0;
+    if (tag == TAG_SPLIT)
+      ctx->split_ms += ms;
+    else
+      ctx->tc_ms += ms;
+    ctx->tag_ms[tag] += ms;
   }
   ctx->ev_used = 0;
   ctx->ev_tag.clear();
@@ -665,6 +682,8 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
         double disc = 0.0, defect = 0.0;
         const unsigned long long seed =
             0x243F6A8885A308D3ull ^ ((unsigned long long)ctx->nd << 40) ^ (unsigned long long)ctx->updates;
+        cudaEvent_t s0 = nullptr, s1 = nullptr;
+        if (ctx->profiling) TRY(ev_pair(ctx, TAG_SPLIT, &s0, &s1));
         if (dir == 0) {
           CKM(subspace_split(ctx->CE, m, n, k, 1, C.site[i + 1], C.dims[i + 1], C.site[i],
                              C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc, &defect));
@@ -672,6 +691,7 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
           CKM(subspace_split(ctx->CE, m, n, k, 0, C.site[i], C.dims[i + 1], C.site[i],
                              C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc, &defect));
         }
+        if (s1) CKM(cudaEventRecord(s1, ctx->st));
         if (!(defect <= 1e-4)) {
           // the FP32 orthonormalisation lost orthogonality (steep or rank-
           // deficient spectrum): take the exact FP64 Jacobi split instead
@@ -1073,6 +1093,8 @@ extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
   o->tc_launches = ctx->tc_launches;
   o->kernel_launches = (long long)__atomic_load_n(&g_xtrg_launches, __ATOMIC_RELAXED);
   o->exact_split_fallbacks = ctx->fallbacks;
+  o->split_ms = ctx->split_ms;
+  o->orth_cluster_calls = (long long)__atomic_load_n(&g_orth_cluster_calls, __ATOMIC_RELAXED);
   return XTRG_OK;
 }
 
@@ -1154,7 +1176,7 @@ extern "C" void xtrg_destroy(xtrg_ctx* ctx) {
   const char* pt = getenv("XTRG_PROFILE_TAGS");
   if (pt && pt[0] == '1') {
     static const char* names[8] = {"other", "substep1 (env x site)", "substep2 (x site)",
-                                   "C_E (split-K)", "env update", "", "", ""};
+                                   "C_E (split-K)", "env update", "truncation (split)", "", ""};
     for (int t = 0; t < 8; ++t)
       if (ctx->tag_n[t])
         fprintf(stderr, "xtrg tc %-24s launches %8lld  %10.1f ms  %8.1f TFLOP/s alg\n", names[t],

@@ -90,3 +90,57 @@ def mpo_to_dense(W) -> np.ndarray:
         T = T.reshape(S * 2, Tt * 2, w.shape[3])
     assert T.shape[2] == 1
     return T[:, :, 0]
+
+
+def dense_bonds(N: int, bonds) -> np.ndarray:
+    """Dense 2^N x 2^N matrix of sum over bonds (i, j, J, Delta) of
+    J (Sx_i Sx_j + Sy_i Sy_j + Delta Sz_i Sz_j) (eq. HeisenbergH on any graph)."""
+    n = 2 ** N
+    H = np.zeros((n, n))
+    ops = {i: (_site_op(SP, i, N), _site_op(SM, i, N), _site_op(SZ, i, N)) for i in range(N)}
+    for (i, j, J, Delta) in bonds:
+        spi, smi, szi = ops[i]
+        spj, smj, szj = ops[j]
+        H += J * (0.5 * (spi @ smj + smi @ spj) + Delta * (szi @ szj))
+    return H
+
+
+def bonds_mpo(N: int, bonds):
+    """MPO of the same bond sum by a distance automaton (App. B.1 with longer
+    range): besides start and stop, one state per (operator, distance d since
+    it was placed) for d = 1 .. R, R the longest bond.  At every site the
+    states shift d -> d+1 and those at the distance of a bond that ends here
+    close with its coupling.  D = 2 + 3 R: larger than necessary for snakes
+    (R = 2W - 1) but direct to check.
+
+    Returns W[i] with shape (Dl, 2, 2, Dr) as xxz_chain_mpo.
+    """
+    R = max(j - i for (i, j, _, _) in bonds)
+    coup = {(i, j): (J, Delta) for (i, j, J, Delta) in bonds}
+    D = 2 + 3 * R
+    start, stop = 0, 1
+
+    def st(o, d):       # o in 0,1,2 = S+, S-, Sz placed d sites ago
+        return 2 + 3 * (d - 1) + o
+
+    first = (SP, SM, SZ)
+    W = []
+    for s_ in range(N):
+        T = np.zeros((D, 2, 2, D))
+        T[start, :, :, start] = ID
+        T[stop, :, :, stop] = ID
+        for o in range(3):
+            T[start, :, :, st(o, 1)] = first[o]
+            for d in range(1, R):
+                T[st(o, d), :, :, st(o, d + 1)] = ID
+            for d in range(1, R + 1):
+                if (s_ - d, s_) in coup:
+                    J, Delta = coup[(s_ - d, s_)]
+                    close = (0.5 * J * SM, 0.5 * J * SP, J * Delta * SZ)[o]
+                    T[st(o, d), :, :, stop] = close
+        if s_ == 0:
+            T = T[start:start + 1]
+        if s_ == N - 1:
+            T = T[:, :, :, stop:stop + 1]
+        W.append(T)
+    return W

@@ -115,7 +115,7 @@ __global__ void sumsq_f64_kernel(const double* __restrict__ a, long long n, doub
 constexpr int PANEL = 32;
 constexpr int ORTH_NT = 256;
 constexpr int ROWS_PER_CTA = 8;
-constexpr int MAX_K = 256;
+constexpr int MAX_K = SUBSPACE_MAX_K;
 constexpr long long ORTH_SPIN_LIMIT = 1LL << 22;
 
 struct OrthArgs {

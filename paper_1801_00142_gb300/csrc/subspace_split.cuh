@@ -22,6 +22,9 @@ struct SubspaceBuffers {
   int* err;            // bounded-wait error flag of the tensor-core GEMM
 };
 
+// Largest k the orthonormalisation handles; wider splits take the exact path.
+constexpr int SUBSPACE_MAX_K = 256;
+
 // Orthonormalisations launched as one thread-block cluster (all contexts).
 extern unsigned long long g_orth_cluster_calls;
 

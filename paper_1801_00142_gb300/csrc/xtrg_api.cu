@@ -684,7 +684,10 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
             0x243F6A8885A308D3ull ^ ((unsigned long long)ctx->nd << 40) ^ (unsigned long long)ctx->updates;
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (ctx->profiling) TRY(ev_pair(ctx, TAG_SPLIT, &s0, &s1));
-        if (dir == 0) {
+        if (k > SUBSPACE_MAX_K) {
+          // wider than the orthonormalisation handles (D* > 256): exact split
+          defect = 1.0;
+        } else if (dir == 0) {
           CKM(subspace_split(ctx->CE, m, n, k, 1, C.site[i + 1], C.dims[i + 1], C.site[i],
                              C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc, &defect));
         } else {

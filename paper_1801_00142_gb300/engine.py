@@ -8,7 +8,7 @@ from __future__ import annotations
 import torch
 
 from . import _lib
-from .hamiltonians import xxz_chain
+from .hamiltonians import xxz_bonds_mpo, xxz_chain
 
 
 class XTRG:
@@ -38,6 +38,13 @@ class XTRG:
     @classmethod
     def xxz(cls, L, J=1.0, Delta=1.0, **kw):
         dims, sites = xxz_chain(L, J, Delta)
+        return cls(dims, sites, **kw)
+
+    @classmethod
+    def from_bonds(cls, N, bonds, **kw):
+        """H = sum over bonds (i, j, J, Delta) on N sites, e.g. a snake-mapped
+        2D lattice (``workloads.square_snake_bonds``)."""
+        dims, sites = xxz_bonds_mpo(N, bonds)
         return cls(dims, sites, **kw)
 
     def init(self):

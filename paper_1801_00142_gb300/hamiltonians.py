@@ -42,3 +42,71 @@ def xxz_chain(L: int, J: float = 1.0, Delta: float = 1.0):
     sites.append(bulk[:, :, :, done:done + 1].copy())
     dims = [1] + [D] * (L - 1) + [1]
     return dims, sites
+
+
+def xxz_bonds_mpo(N: int, bonds):
+    """MPO of H = sum over bonds (i, j, J, Delta), i < j, of
+    J (Sx_i Sx_j + Sy_i Sy_j + Delta Sz_i Sz_j), for two-body couplings of any
+    range (the snake-mapped 2D lattices of Sec. I).
+
+    The automaton keeps, across each cut between sites c and c+1, one pending
+    state per (left site l with a bond reaching past the cut, operator of l):
+    the bond space at cut c is [done, (l, S+), (l, S-), (l, Sz) for each such
+    l, ready], so D = 2 + 3 |open sites|, which is 5 for a chain and 3W + 2
+    for a width-W snake with open boundaries.  At site c+1 a pending state
+    either continues (identity) or closes with the partner operator and its
+    coupling, or both when l has bonds on both sides of c+1.
+
+    Returns (bond_dims, sites) like xxz_chain.
+    """
+    if N < 2:
+        raise ValueError("need N >= 2")
+    terms = {}
+    for (i, j, J, Delta) in bonds:
+        if not (0 <= i < j < N):
+            raise ValueError(f"bad bond {(i, j)}")
+        terms[(i, j)] = (float(J), float(Delta))
+    last = {}          # last partner of every left site
+    for (i, j) in terms:
+        last[i] = max(last.get(i, -1), j)
+    # open[c]: left sites with a bond crossing the cut after site c
+    opened = [sorted(l for l, r in last.items() if l <= c < r) for c in range(N - 1)]
+    partner = {"+": _SM, "-": _SP, "z": _SZ}
+    first = {"+": _SP, "-": _SM, "z": _SZ}
+    ops = ("+", "-", "z")
+
+    def states(c):
+        """index map of the bond space at cut c"""
+        m = {"done": 0}
+        for l in opened[c]:
+            for o in ops:
+                m[(l, o)] = len(m)
+        m["ready"] = len(m)
+        return m
+
+    cuts = [states(c) for c in range(N - 1)]
+    sites = []
+    for s_ in range(N):
+        left = cuts[s_ - 1] if s_ > 0 else {"ready": 0}
+        right = cuts[s_] if s_ < N - 1 else {"done": 0}
+        Wt = np.zeros((len(left), 2, 2, len(right)))
+        if "done" in left and "done" in right:
+            Wt[left["done"], :, :, right["done"]] = _I
+        if "ready" in left and "ready" in right:
+            Wt[left["ready"], :, :, right["ready"]] = _I
+        for o in ops:
+            if "ready" in left and (s_, o) in right:          # place the first operator
+                Wt[left["ready"], :, :, right[(s_, o)]] = first[o]
+        for key, a in left.items():
+            if not isinstance(key, tuple):
+                continue
+            l, o = key
+            if key in right:                                  # carry it past this site
+                Wt[a, :, :, right[key]] = _I
+            if (l, s_) in terms and "done" in right:           # close it here
+                J, Delta = terms[(l, s_)]
+                g = J * Delta if o == "z" else 0.5 * J
+                Wt[a, :, :, right["done"]] += g * partner[o]
+        sites.append(Wt)
+    dims = [1] + [len(c) for c in cuts] + [1]
+    return dims, sites

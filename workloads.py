@@ -98,3 +98,92 @@ def small_cases() -> List[ChainWorkload]:
         ChainWorkload(name="xxx_L10_trunc", L=10, Delta=1.0, tau0=2.0 ** -8, dstar=24,
                       sweeps=2, n_doublings=10),
     ]
+
+
+# ------------------------------------------------------------------ lattices
+# Two-dimensional lattices mapped to a snake path (Sec. I: a width-W system
+# becomes a chain with bonds up to distance 2W - 1).  Site (x, y), x along the
+# length, y across the width, has index x*W + y on even columns and
+# x*W + (W-1-y) on odd columns, so consecutive sites along the path are
+# neighbours.  A bond list is a list of (i, j, J, Delta) with i < j: the
+# coupling J (Sx Sx + Sy Sy + Delta Sz Sz) between path sites i and j.  These
+# are model descriptions only (no Hamiltonian arithmetic).
+
+def snake_index(x: int, y: int, W: int) -> int:
+    return x * W + (y if x % 2 == 0 else W - 1 - y)
+
+
+def _bond(i: int, j: int, J: float, Delta: float):
+    return (min(i, j), max(i, j), float(J), float(Delta))
+
+
+def chain_bonds(L: int, J: float = 1.0, Delta: float = 1.0):
+    """Open chain: nearest-neighbour bonds (i, i+1)."""
+    return [(i, i + 1, float(J), float(Delta)) for i in range(L - 1)]
+
+
+def square_snake_bonds(W: int, Lx: int, J: float = 1.0, Delta: float = 1.0):
+    """W x Lx square lattice, open boundaries in both directions."""
+    bonds = []
+    for x in range(Lx):
+        for y in range(W):
+            i = snake_index(x, y, W)
+            if y + 1 < W:
+                bonds.append(_bond(i, snake_index(x, y + 1, W), J, Delta))
+            if x + 1 < Lx:
+                bonds.append(_bond(i, snake_index(x + 1, y, W), J, Delta))
+    return sorted(bonds)
+
+
+def triangular_yc_bonds(W: int, Lx: int, J: float = 1.0, Delta: float = 1.0):
+    """Triangular lattice on a YC cylinder: periodic across the width W (one
+    lattice direction wraps the circumference), open along the length Lx.
+    Each site (x, y) couples to (x, y+1 mod W), (x+1, y) and (x+1, y-1 mod W)."""
+    if W < 3:
+        raise ValueError("a YC cylinder needs W >= 3")
+    bonds = set()
+    for x in range(Lx):
+        for y in range(W):
+            i = snake_index(x, y, W)
+            bonds.add(_bond(i, snake_index(x, (y + 1) % W, W), J, Delta))
+            if x + 1 < Lx:
+                bonds.add(_bond(i, snake_index(x + 1, y, W), J, Delta))
+                bonds.add(_bond(i, snake_index(x + 1, (y - 1) % W, W), J, Delta))
+    return sorted(bonds)
+
+
+@dataclass(frozen=True)
+class LatticeWorkload:
+    """One XTRG run on a snake-mapped 2D lattice (kind "square": open W x Lx;
+    "triangular_yc": YC cylinder of circumference W and length Lx)."""
+
+    name: str
+    kind: str
+    W: int
+    Lx: int
+    J: float = 1.0
+    Delta: float = 1.0
+    tau0: float = 2.0 ** -10
+    order: int = 4
+    dstar: int = 500
+    sweeps: int = 4
+    n_doublings: int = 15
+    n_grids: int = 1
+
+    @property
+    def N(self) -> int:
+        return self.W * self.Lx
+
+    def bonds(self):
+        gen = square_snake_bonds if self.kind == "square" else triangular_yc_bonds
+        return gen(self.W, self.Lx, self.J, self.Delta)
+
+
+# 6 x 6 open square Heisenberg lattice, tau0 = 2^-10 doubled to beta = 32, D* = 500.
+SQUARE_6X6 = LatticeWorkload(name="square_6x6_D500", kind="square", W=6, Lx=6, dstar=500)
+# Triangular Heisenberg 6 x 6 YC cylinder and the easy-plane (Delta = 0.5) 8 x 8
+# square lattice, D* = 768, 4 interleaved tau0 grids each.
+TRIANGULAR_YC6X6 = LatticeWorkload(name="triangular_yc6x6_D768", kind="triangular_yc", W=6, Lx=6,
+                                   dstar=768, n_grids=4)
+SQUARE_8X8_XXZ = LatticeWorkload(name="square_8x8_xxz_D768", kind="square", W=8, Lx=8,
+                                 Delta=0.5, dstar=768, n_grids=4)

@@ -333,3 +333,29 @@ def run_xtrg(H, tau0, order, dstar, sweeps, n_doublings, rel_tol, init_sweeps=No
         if keep_states:
             states.append(([w.copy() for w in rho], lnc))
     return (rows, states) if keep_states else rows
+
+
+def mpo_entanglement(W):
+    """MPO entanglement per bond (Sec. IV, Eq. purif): the MPO of rho is read
+    as a state with doubled local spaces; at each bond its Schmidt values s_i
+    give r_i = s_i^2 / sum s^2 and S_E = -sum r_i ln r_i.  Computed by a
+    right-to-left QR pass followed by a left-to-right pass of SVDs of the
+    orthogonality centre.  Returns a list of L-1 entropies (bond i between
+    sites i and i+1)."""
+    W = [w.copy() for w in W]
+    L = len(W)
+    for i in range(L - 1, 0, -1):
+        l, s, t, r = W[i].shape
+        Q, R = np.linalg.qr(W[i].reshape(l, s * t * r).T)       # W_i^T = Q R
+        W[i] = Q.T.reshape(-1, s, t, r)
+        W[i - 1] = np.tensordot(W[i - 1], R.T, axes=([3], [0]))
+    out = []
+    for i in range(L - 1):
+        l, s, t, r = W[i].shape
+        U, S, Vt = np.linalg.svd(W[i].reshape(l * s * t, r), full_matrices=False)
+        p = S ** 2 / np.sum(S ** 2)
+        p = p[p > 0]
+        out.append(float(-np.sum(p * np.log(p))))
+        W[i] = U.reshape(l, s, t, -1)
+        W[i + 1] = np.tensordot(np.diag(S) @ Vt, W[i + 1], axes=([1], [0]))
+    return out

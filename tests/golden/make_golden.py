@@ -21,7 +21,19 @@ from oracle import xtrg as xo  # noqa: E402
 
 def _run(w, H):
     return xo.run_xtrg(H, w.tau0, w.order, w.dstar, w.sweeps, w.n_doublings,
-                       w.svd_rel_tol, init_sweeps=w.init_sweeps)
+                       w.svd_rel_tol, init_sweeps=_init_sweeps(w))
+
+
+def hamiltonian(w):
+    """The oracle's MPO of a workload: the chain automaton, or for a lattice
+    the distance automaton of its snake bond list."""
+    if isinstance(w, wl.LatticeWorkload):
+        return hm.bonds_mpo(w.N, w.bonds())
+    return hm.xxz_chain_mpo(w.L, w.J, w.Delta)
+
+
+def _init_sweeps(w):
+    return getattr(w, "init_sweeps", None) or w.sweeps
 
 
 def run(w):
@@ -31,7 +43,7 @@ def run(w):
     D* cuts through a degenerate set of singular values, so a parity bar
     below this sensitivity would be meaningless)."""
     import numpy as np
-    H = hm.xxz_chain_mpo(w.L, w.J, w.Delta)
+    H = hamiltonian(w)
     t = time.time()
     rows = _run(w, H)
     secs = time.time() - t
@@ -51,7 +63,7 @@ def run(w):
 
 
 def main(names):
-    cases = {w.name: w for w in wl.small_cases() + [wl.CHAIN_L8]}
+    cases = {w.name: w for w in wl.small_cases() + [wl.CHAIN_L8] + wl.small_lattice_cases()}
     for name in names or list(cases):
         out = run(cases[name])
         with open(os.path.join(HERE, f"oracle_{name}.json"), "w") as f:

@@ -109,3 +109,24 @@ def test_oracle_xtrg_on_square_snake_matches_ed():
         ref = ex.ed_thermo(E, r["beta"], N)
         assert abs(r["lnZ"] - ref["lnZ"]) <= 1e-10 * max(1.0, abs(ref["lnZ"]))
         assert abs(r["u"] - ref["u"]) <= 1e-9
+
+
+def test_golden_snake_rows_match_ed():
+    """The stored oracle rows of the untruncated snake cases equal exact
+    diagonalisation (pins the golden files the GPU parity tests read)."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    for w in wl.small_lattice_cases():
+        with open(os.path.join(here, f"oracle_{w.name}.json")) as f:
+            gd = json.load(f)
+        E = ex.ed_spectrum(oh.dense_bonds(w.N, w.bonds()))
+        for r in gd["rows"]:
+            ref = ex.ed_thermo(E, r["beta"], w.N)
+            if gd["truncated"]:
+                # truncation discards weight of the compressed products: for this
+                # case ln Z stays at or below the exact value at every beta
+                assert r["lnZ"] <= ref["lnZ"] + 1e-9
+            else:
+                assert abs(r["lnZ"] - ref["lnZ"]) <= 1e-10 * max(1.0, abs(ref["lnZ"]))
+                assert abs(r["u"] - ref["u"]) <= 1e-9

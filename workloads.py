@@ -169,6 +169,7 @@ class LatticeWorkload:
     sweeps: int = 4
     n_doublings: int = 15
     n_grids: int = 1
+    svd_rel_tol: float = 1e-15
 
     @property
     def N(self) -> int:
@@ -187,3 +188,17 @@ TRIANGULAR_YC6X6 = LatticeWorkload(name="triangular_yc6x6_D768", kind="triangula
                                    dstar=768, n_grids=4)
 SQUARE_8X8_XXZ = LatticeWorkload(name="square_8x8_xxz_D768", kind="square", W=8, Lx=8,
                                  Delta=0.5, dstar=768, n_grids=4)
+
+
+def small_lattice_cases() -> List[LatticeWorkload]:
+    """Snake-lattice parity cases the oracle finishes in seconds: an
+    untruncated and a truncated open square strip and an untruncated
+    triangular YC cylinder, tau0 = 2^-10 doubled to beta = 4."""
+    return [
+        LatticeWorkload(name="square_2x3", kind="square", W=2, Lx=3, dstar=64, sweeps=2,
+                        n_doublings=12),
+        LatticeWorkload(name="square_2x3_trunc", kind="square", W=2, Lx=3, dstar=20, sweeps=2,
+                        n_doublings=12),
+        LatticeWorkload(name="triangular_yc3x2", kind="triangular_yc", W=3, Lx=2, dstar=64,
+                        sweeps=2, n_doublings=12),
+    ]

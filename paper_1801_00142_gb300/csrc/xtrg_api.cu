@@ -949,17 +949,20 @@ extern "C" xtrg_status xtrg_init(xtrg_ctx* ctx) {
   for (int i = 0; i <= L; ++i) ctx->Y.dims[i] = 1;
   for (int i = 0; i < L; ++i) CK(dev_identity_site(ctx->Y.site[i], ctx->st));
   for (int k = ctx->cfg.order; k >= 1; --k) {
-    // guess: the exact product H^T Y with fused bonds
-    for (int i = 0; i <= L; ++i) {
-      if (ctx->Y.dims[i] > ctx->plan.cap_fat)
-        return fail(ctx, XTRG_ENOMEM, "series term bond %d exceeds the initial-guess capacity %d",
-                    ctx->Y.dims[i], ctx->plan.cap_fat);
-      ctx->fat.dims[i] = ctx->H.dims[i] * ctx->Y.dims[i];
+    bool fat_fits = true;
+    for (int i = 0; i <= L; ++i) fat_fits = fat_fits && ctx->Y.dims[i] <= ctx->plan.cap_fat;
+    if (fat_fits) {
+      // guess: the exact product H^T Y with fused bonds
+      for (int i = 0; i <= L; ++i) ctx->fat.dims[i] = ctx->H.dims[i] * ctx->Y.dims[i];
+      for (int i = 0; i < L; ++i)
+        CK(mpo_exact_product(ctx->H.site[i], ctx->H.dims[i], ctx->H.dims[i + 1], ctx->Y.site[i],
+                             ctx->Y.dims[i], ctx->Y.dims[i + 1], ctx->fat.site[i], ctx->st));
+      TRY(canonicalize(ctx, ctx->fat.dims, ctx->fat.site, ctx->C));
+    } else {
+      // the fused bonds would exceed the guess capacity (long-range H such as
+      // a 2D snake, with Y near D*): the sweeps start from Y, right-canonical
+      TRY(canonicalize(ctx, ctx->Y.dims, ctx->Y.site, ctx->C));
     }
-    for (int i = 0; i < L; ++i)
-      CK(mpo_exact_product(ctx->H.site[i], ctx->H.dims[i], ctx->H.dims[i + 1], ctx->Y.site[i],
-                           ctx->Y.dims[i], ctx->Y.dims[i + 1], ctx->fat.site[i], ctx->st));
-    TRY(canonicalize(ctx, ctx->fat.dims, ctx->fat.site, ctx->C));
     TRY(compress(ctx, ctx->H, ctx->Y, ctx->C, ctx->cfg.dstar, ctx->cfg.init_sweeps));
     // Y <- I + (-tau0/k) * (H Y)
     const double alpha = -ctx->cfg.tau0 / k;

@@ -192,6 +192,28 @@ xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int
 xtrg_status xtrg_tc_gemm_static(const double* A, const double* B, double* C, int M, int N, int K,
                                 int batch, int planes, int nprod, int splitk, void* cuda_stream);
 
+/* ------------------------------------------------------------------ batch
+ * Many independent runs on one GPU: interleaved tau0 grids of one model
+ * (Eq. zshift) or different (L, Delta, D*) instances.  The workspace is cut
+ * into equal slots of xtrg_batch_plan's slot_bytes (the largest instance's
+ * need, rounded up to 256 bytes); min(n, max_concurrent (<= 0: 8), slots
+ * that fit) host threads each own one slot and one stream and take instances
+ * from a shared queue, largest first.  Instance i runs xtrg_init and
+ * n_doublings[i] doublings; its n_doublings[i] + 1 observables rows (beta =
+ * tau0 ... 2^n tau0) go to out[off_i ...], off_i = sum_{j<i} (n_doublings[j]
+ * + 1).  H, cfg, n_doublings: n host entries, read only; workspace: device
+ * memory, 256-byte aligned, borrowed for the call.  The caller's stream is
+ * ordered before the first and after the last device work.  On the first
+ * failing instance no new instance starts; the call returns that status and
+ * xtrg_last_error(NULL) holds its message. */
+xtrg_status xtrg_batch_plan(int n, const xtrg_mpo* H, const xtrg_config* cfg,
+                            size_t workspace_bytes, int max_concurrent, int* n_slots,
+                            size_t* slot_bytes);
+xtrg_status xtrg_batch_run(int n, const xtrg_mpo* H, const xtrg_config* cfg,
+                           const int* n_doublings, xtrg_obs* out, void* workspace,
+                           size_t workspace_bytes, int max_concurrent, void* cuda_stream);
+
+/* Message of the last failure of ctx; with ctx == NULL, of the last batch call. */
 const char* xtrg_last_error(const xtrg_ctx* ctx);
 
 /* Free host bookkeeping.  The workspace stays the caller's. */

@@ -25,7 +25,7 @@ SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "x
            "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_get_stats",
            "xtrg_set_profiling",
            "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm",
-           "xtrg_tc_gemm_static"]
+           "xtrg_tc_gemm_static", "xtrg_batch_plan", "xtrg_batch_run"]
 
 
 class xtrg_mpo(C.Structure):
@@ -94,6 +94,14 @@ def _load():
     lib.xtrg_get_stats.argtypes = [P, C.POINTER(xtrg_stats)]
     lib.xtrg_set_profiling.restype = C.c_int
     lib.xtrg_set_profiling.argtypes = [P, C.c_int]
+    lib.xtrg_batch_plan.restype = C.c_int
+    lib.xtrg_batch_plan.argtypes = [C.c_int, C.POINTER(xtrg_mpo), C.POINTER(xtrg_config),
+                                    C.c_size_t, C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_size_t)]
+    lib.xtrg_batch_run.restype = C.c_int
+    lib.xtrg_batch_run.argtypes = [C.c_int, C.POINTER(xtrg_mpo), C.POINTER(xtrg_config),
+                                   C.POINTER(C.c_int), C.POINTER(xtrg_obs), P, C.c_size_t,
+                                   C.c_int, P]
     lib.xtrg_last_error.restype = C.c_char_p
     lib.xtrg_last_error.argtypes = [P]
     lib.xtrg_destroy.restype = None
@@ -217,6 +225,41 @@ def xtrg_tc_gemm_static(A_ptr, B_ptr, C_ptr, M, N, K, batch, planes, nprod, spli
     returns the status code unchanged so callers can see XTRG_ENOMEM."""
     return int(LIB.xtrg_tc_gemm_static(C.c_void_p(A_ptr), C.c_void_p(B_ptr), C.c_void_p(C_ptr),
                                        M, N, K, batch, planes, nprod, splitk, C.c_void_p(stream)))
+
+
+def _batch_arrays(Hs, cfgs):
+    n = len(Hs)
+    if n != len(cfgs) or n == 0:
+        raise ValueError("one configuration per Hamiltonian, at least one instance")
+    H_arr = (xtrg_mpo * n)(*[h.struct for h in Hs])
+    c_arr = (xtrg_config * n)(*cfgs)
+    return n, H_arr, c_arr
+
+
+def xtrg_batch_plan(Hs, cfgs, workspace_bytes, max_concurrent=0):
+    """(n_slots, slot_bytes) of a batch in a workspace of the given size."""
+    n, H_arr, c_arr = _batch_arrays(Hs, cfgs)
+    slots, sb = C.c_int(0), C.c_size_t(0)
+    st = LIB.xtrg_batch_plan(n, H_arr, c_arr, workspace_bytes, max_concurrent, C.byref(slots),
+                             C.byref(sb))
+    if st != XTRG_OK:
+        raise XtrgError(st, LIB.xtrg_last_error(None).decode())
+    return slots.value, sb.value
+
+
+def xtrg_batch_run(Hs, cfgs, n_doublings, ws_ptr, ws_bytes, max_concurrent, stream):
+    """Rows of observables per instance (list of lists of dicts)."""
+    n, H_arr, c_arr = _batch_arrays(Hs, cfgs)
+    nd = (C.c_int * n)(*[int(x) for x in n_doublings])
+    out = (xtrg_obs * sum(int(x) + 1 for x in n_doublings))()
+    st = LIB.xtrg_batch_run(n, H_arr, c_arr, nd, out, ws_ptr, ws_bytes, max_concurrent, stream)
+    if st != XTRG_OK:
+        raise XtrgError(st, LIB.xtrg_last_error(None).decode())
+    rows, k = [], 0
+    for x in n_doublings:
+        rows.append([out[k + j].as_dict() for j in range(int(x) + 1)])
+        k += int(x) + 1
+    return rows
 
 
 def xtrg_last_error(ctx) -> str:

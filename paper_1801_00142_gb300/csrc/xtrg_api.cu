@@ -1173,8 +1173,10 @@ extern "C" xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C,
   return h ? XTRG_ETIMEOUT : XTRG_OK;
 }
 
+const char* xtrg_batch_last_error();   // batch.cu
+
 extern "C" const char* xtrg_last_error(const xtrg_ctx* ctx) {
-  return ctx ? ctx->err.c_str() : "null context";
+  return ctx ? ctx->err.c_str() : xtrg_batch_last_error();
 }
 
 extern "C" void xtrg_destroy(xtrg_ctx* ctx) {

@@ -46,15 +46,6 @@ struct GemmF64 {
 
 cudaError_t gemm_f64(const GemmF64& g, cudaStream_t st);
 
-// The same contract in FP32 (small contractions of the tensor-core path's truncation).
-struct GemmF32 {
-  int M, N, K, batch;
-  const float* A; Idx3 am, ak; long long sab;
-  const float* B; Idx3 bk, bn; long long sbb;
-  float* C; Idx3 cm, cn; long long scb;
-  double alpha, beta;
-};
-cudaError_t gemm_f32(const GemmF32& g, cudaStream_t st);
 
 // ---------------------------------------------------------------- SVD split
 // One-sided (Hestenes) Jacobi SVD of a row-major m x n matrix M in FP64,

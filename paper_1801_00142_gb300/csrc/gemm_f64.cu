@@ -6,8 +6,8 @@
 // contraction indices are up to three-level strided views of the stored
 // tensors (struct Idx3), so no permutation pass is needed between steps.
 //
-// This is the FP64 path (and, instantiated for float, the small FP32
-// contractions of the tensor-core path's truncation).  On GB300 the FP64 rate
+// This is the FP64 path; it also serves the canonicalisation and the traces
+// of the tensor-core path.  On GB300 the FP64 rate
 // is a small fraction of the FP32 rate, so the FP64 kernel is bound by FP64
 // issue: a 64x64 output tile per 256-thread CTA, 4x4 outputs per thread, k
 // staged 16 at a time through shared memory, with the per-tile view offsets
@@ -127,4 +127,3 @@ cudaError_t launch(const G& g, cudaStream_t st) {
 }  // namespace
 
 cudaError_t gemm_f64(const GemmF64& g, cudaStream_t st) { return launch<double>(g, st); }
-cudaError_t gemm_f32(const GemmF32& g, cudaStream_t st) { return launch<float>(g, st); }

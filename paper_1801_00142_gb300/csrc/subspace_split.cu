@@ -29,6 +29,8 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "mixed_ops.cuh"
 #include "subspace_split.cuh"
@@ -70,12 +72,6 @@ __global__ void add_noise_kernel(float* __restrict__ Y, long long n, float eta,
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
     Y[e] += eta * hash_uniform(seed ^ (0xD1B54A32D192ED03ull * (e + 1)));
-}
-
-__global__ void copy_d2f_kernel(const double* __restrict__ a, long long n, float* __restrict__ b) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x)
-    b[e] = (float)a[e];
 }
 
 __global__ void copy_f2d_kernel(const float* __restrict__ a, long long n, double* __restrict__ b) {
@@ -520,7 +516,8 @@ __global__ void __launch_bounds__(OC_NT, 1) orth_cluster(OrthClusterArgs a) {
   cluster.sync();
 }
 
-int g_orth_cluster_state = 0;   // 0 unknown, 1 available, -1 unavailable
+// cleared when a cluster launch fails: the grid-wide kernel is used from then on
+std::atomic<int> g_orth_cluster_ok{1};
 
 // Launch configuration of orth_cluster (one cluster of OC_NC CTAs).
 cudaLaunchConfig_t orth_cluster_config(size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
@@ -541,38 +538,44 @@ cudaLaunchConfig_t orth_cluster_config(size_t smem, cudaStream_t st, cudaLaunchA
 // Whether one cluster of OC_NC CTAs with the largest shared-memory request
 // can be resident on this device (asked once; no kernel runs for it).
 bool orth_cluster_available() {
-  if (g_orth_cluster_state != 0) return g_orth_cluster_state > 0;
-  g_orth_cluster_state = -1;
-  const size_t smem = orth_cluster_smem(MAX_K);
-  if (cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = orth_cluster_config(smem, 0, attr);
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, orth_cluster, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (nclusters >= 1) g_orth_cluster_state = 1;
-  return g_orth_cluster_state > 0;
+  static const bool avail = []() {
+    const size_t smem = orth_cluster_smem(MAX_K);
+    if (cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = orth_cluster_config(smem, 0, attr);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, orth_cluster, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return nclusters >= 1;
+  }();
+  return avail && g_orth_cluster_ok.load(std::memory_order_relaxed) != 0;
 }
 
-int g_orth_max_ctas = 0;
-
-GemmF32 g32(int M, int N, int K, const float* A, Idx3 am, Idx3 ak, const float* B, Idx3 bk,
-            Idx3 bn, float* C, Idx3 cm, Idx3 cn) {
-  GemmF32 g;
-  g.M = M; g.N = N; g.K = K; g.batch = 1;
-  g.A = A; g.am = am; g.ak = ak; g.sab = 0;
-  g.B = B; g.bk = bk; g.bn = bn; g.sbb = 0;
-  g.C = C; g.cm = cm; g.cn = cn; g.scb = 0;
-  g.alpha = 1.0; g.beta = 0.0;
-  return g;
+// CTAs of the grid-wide kernel's cooperative launch (one-time, thread-safe)
+struct OrthSetup {
+  cudaError_t err;
+  int max_ctas;
+};
+const OrthSetup& orth_setup() {
+  static const OrthSetup s = []() {
+    OrthSetup r{cudaSuccess, 0};
+    int dev = 0, sms = 0, per = 0;
+    r.err = cudaGetDevice(&dev);
+    if (r.err == cudaSuccess) r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (r.err == cudaSuccess)
+      r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, orth_persistent, ORTH_NT, 0);
+    r.max_ctas = sms * per;
+    return r;
+  }();
+  return s;
 }
 
 #define RET(x)                                 \
@@ -599,17 +602,12 @@ cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaS
     }
     // the cluster could not be launched: use the grid-wide kernel from now on
     cudaGetLastError();
-    g_orth_cluster_state = -1;
+    g_orth_cluster_ok.store(0, std::memory_order_relaxed);
   }
   const int G = (rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
-  if (g_orth_max_ctas == 0) {
-    int dev = 0, sms = 0, per = 0;
-    RET(cudaGetDevice(&dev));
-    RET(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    RET(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, orth_persistent, ORTH_NT, 0));
-    g_orth_max_ctas = sms * per;
-  }
-  if (G > g_orth_max_ctas || G > b.orth_max_ctas) return cudaErrorInvalidValue;
+  const OrthSetup& setup = orth_setup();
+  RET(setup.err);
+  if (G > setup.max_ctas || G > b.orth_max_ctas) return cudaErrorInvalidValue;
   OrthArgs a;
   a.Y = Y; a.rows = rows; a.k = k;
   a.part = b.orth_part; a.red = b.orth_red;

@@ -235,7 +235,25 @@ __global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
   }
 }
 
-int g_max_ctas = 0;
+// CTAs of the cooperative launch (one-time, thread-safe initialisation)
+struct SvdSetup {
+  cudaError_t err;
+  int max_ctas;
+};
+const SvdSetup& svd_setup() {
+  static const SvdSetup s = []() {
+    SvdSetup r{cudaSuccess, 0};
+    int dev = 0, sms = 0, per = 0;
+    r.err = cudaGetDevice(&dev);
+    if (r.err == cudaSuccess) r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (r.err == cudaSuccess)
+      r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, svd_persistent, NT, 0);
+    r.max_ctas = sms * (per < 2 ? per : 2);
+    if (r.err == cudaSuccess && r.max_ctas < 1) r.err = cudaErrorLaunchOutOfResources;
+    return r;
+  }();
+  return s;
+}
 
 }  // namespace
 
@@ -250,17 +268,9 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
       ncols > buf.max_cols)
     return cudaErrorInvalidValue;
   cudaError_t e;
-  if (g_max_ctas == 0) {
-    int dev = 0, sms = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, svd_persistent, NT, 0)) !=
-        cudaSuccess)
-      return e;
-    g_max_ctas = sms * (per < 2 ? per : 2);
-    if (g_max_ctas < 1) return cudaErrorLaunchOutOfResources;
-  }
+  const SvdSetup& setup = svd_setup();
+  if (setup.err != cudaSuccess) return setup.err;
+  const int max_ctas = setup.max_ctas;
   SvdArgs a;
   a.M = M; a.m = m; a.n = n; a.trans = trans; a.len = len; a.ncols = ncols;
   a.nn = ncols + (ncols & 1);
@@ -280,7 +290,7 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
   int grid = (pairs + WPB - 1) / WPB;
   long long work = (long long)len * ncols / (NT * 8);
   if (work > grid) grid = (int)work;
-  if (grid > g_max_ctas) grid = g_max_ctas;
+  if (grid > max_ctas) grid = max_ctas;
   if (grid < 1) grid = 1;
   void* args[] = {&a};
   note_launch();

@@ -438,17 +438,38 @@ typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void
                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                              CUtensorMapFloatOOBfill);
 
+// One-time lookups (function-local statics: initialised once, thread-safe,
+// so contexts driven from several host threads share them safely).
 EncodeFn get_encode() {
-  static EncodeFn fn = nullptr;
-  if (!fn) {
+  static const EncodeFn fn = []() -> EncodeFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeFn)p;
-  }
+      return (EncodeFn)p;
+    return nullptr;
+  }();
   return fn;
+}
+
+// the kernel's shared-memory opt-in and the SM count of the current device
+struct LaunchSetup {
+  cudaError_t err;
+  int sms;
+};
+const LaunchSetup& launch_setup() {
+  static const LaunchSetup s = []() {
+    LaunchSetup r{cudaSuccess, 0};
+    int dev = 0;
+    r.err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024);
+    if (r.err == cudaSuccess) r.err = cudaGetDevice(&dev);
+    if (r.err == cudaSuccess)
+      r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
+    return r;
+  }();
+  return s;
 }
 
 // 4-D map: (k, rows, batch, plane), box (64, 128, 1, 1), 128-byte swizzle,
@@ -509,20 +530,9 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   if ((e = make_map(&ma, A)) != cudaSuccess) return e;
   if ((e = make_map(&mb, B)) != cudaSuccess) return e;
   const int smem = S * stage_bytes + 1024 + (2 * S + 5) * 8 + 8 + 4 * BN * 8 + 64;
-  static bool attr_done = false;
-  if (!attr_done) {
-    if ((e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  227 * 1024)) != cudaSuccess)
-      return e;
-    attr_done = true;
-  }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
-  }
+  const LaunchSetup& setup = launch_setup();
+  if (setup.err != cudaSuccess) return setup.err;
+  const int sms = setup.sms;
   const long long tiles =
       (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * (long long)batch * splitk;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;

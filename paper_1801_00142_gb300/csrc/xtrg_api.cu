@@ -412,12 +412,11 @@ xtrg_status normalize(xtrg_ctx* ctx, DevMpo& C, double* lns) {
 // Debug mode (environment XTRG_DEBUG=1): after each step of a product, scan
 // the FP64 result for non-finite values and name the first step that made one.
 bool debug_on() {
-  static int v = -1;
-  if (v < 0) {
+  static const bool v = []() {
     const char* e = getenv("XTRG_DEBUG");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v == 1;
+    return e && e[0] == '1';
+  }();
+  return v;
 }
 
 xtrg_status debug_check(xtrg_ctx* ctx, const char* what, const double* p, long long n, int i) {

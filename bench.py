@@ -37,6 +37,8 @@ UNIT = "doubling steps/s"
 W = wl.CHAIN_L64_XXX
 DESC = ("Heisenberg XXX chain, L=64 open, J=1, Delta=1, D*=256, 4 sweeps/doubling, "
         "tau0=2^-12 doubled to beta=64; the last steps of that schedule are timed")
+L2_NOTE = ("no flush: every update streams operands far larger than L2 (one environment "
+           "~100 MB, one resident half ~400 MB per plane set; ~75 GB working set)")
 
 
 def set_workload(L, dstar):
@@ -164,7 +166,9 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": t * updates * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": DESC, "L": W.L, "dstar": W.dstar, "sweeps": W.sweeps},
+           "config": {"workload": DESC, "L": W.L, "dstar": W.dstar, "sweeps": W.sweeps,
+                      "tau0": W.tau0, "prec": "fp64 (oracle)", "l2": L2_NOTE,
+                      "parallelism": "rank 0 only"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                             "sample": f"one oracle two-site update per step at bond 256, median "
                                       f"{t:.3f} s, x{updates} updates per doubling"},
@@ -285,7 +289,7 @@ def run_native(args):
            "config": {"workload": DESC, "L": W.L, "dstar": W.dstar, "sweeps": W.sweeps,
                       "tau0": W.tau0, "prec": args.prec,
                       "beta": [rows[0]["beta"], rows[-1]["beta"]],
-                      "l2": "inputs larger than L2 (environments ~7 GB, parts ~1.6 GB per update)",
+                      "l2": L2_NOTE,
                       "parallelism": f"replicas x{ws}"},
            "tflops": contr / (ms / 1e3) / 1e12 * ws,
            "tflops_note": "algorithmic 2MNK of the contraction GEMMs per second (whole job)",

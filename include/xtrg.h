@@ -33,7 +33,9 @@
  * - Errors: every call returns an xtrg_status; no exception or abort crosses
  *   the ABI.  After a failure xtrg_last_error(ctx) holds a one-line message.
  *   A context that returned XTRG_ECUDA should be destroyed.
- * - Thread safety: a context must not be used from two threads at once.
+ * - Thread safety: a context must not be used from two threads at once;
+ *   different contexts (each with its own workspace and stream) may be driven
+ *   from different host threads concurrently, as xtrg_batch_run does.
  */
 #ifndef XTRG_H
 #define XTRG_H

@@ -3,10 +3,34 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 // Number of kernels this library has launched (all contexts, all streams);
 // every launch site calls note_launch().
 extern unsigned long long g_xtrg_launches;
 static inline void note_launch() { __atomic_add_fetch(&g_xtrg_launches, 1ull, __ATOMIC_RELAXED); }
+
+// One-time set-up per device (kernel attributes, SM counts, occupancy): the
+// first call on a device runs make(dev) with that device current and keeps
+// its result; later calls on the same device return the kept value.  Safe to
+// call from several host threads.  Function attributes set by cudaFuncSetAttribute
+// belong to the device that was current, so they must be set once on each.
+constexpr int XTRG_MAX_DEVICES = 64;
+template <typename T>
+struct PerDevice {
+  std::once_flag once[XTRG_MAX_DEVICES];
+  T val[XTRG_MAX_DEVICES];
+  template <typename F>
+  cudaError_t get(F make, T* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= XTRG_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [&]() { val[dev] = make(dev); });
+    *out = val[dev];
+    return cudaSuccess;
+  }
+};
 
 // A strided view of one GEMM index.  The index idx in [0, n2*n1*n0) is split
 // as idx = (i2*n1 + i1)*n0 + i0 and lands at element offset

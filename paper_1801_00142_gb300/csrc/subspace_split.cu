@@ -536,45 +536,57 @@ cudaLaunchConfig_t orth_cluster_config(size_t smem, cudaStream_t st, cudaLaunchA
 }
 
 // Whether one cluster of OC_NC CTAs with the largest shared-memory request
-// can be resident on this device (asked once; no kernel runs for it).
+// can be resident on the current device (asked once per device; no kernel
+// runs for it).
+PerDevice<bool> g_orth_cluster_avail;
+
 bool orth_cluster_available() {
-  static const bool avail = []() {
-    const size_t smem = orth_cluster_smem(MAX_K);
-    if (cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = orth_cluster_config(smem, 0, attr);
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, orth_cluster, &cfg) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    return nclusters >= 1;
-  }();
+  bool avail = false;
+  if (g_orth_cluster_avail.get(
+          [](int) {
+            const size_t smem = orth_cluster_smem(MAX_K);
+            if (cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                     1) != cudaSuccess ||
+                cudaFuncSetAttribute(orth_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess) {
+              cudaGetLastError();
+              return false;
+            }
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = orth_cluster_config(smem, 0, attr);
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, orth_cluster, &cfg) != cudaSuccess) {
+              cudaGetLastError();
+              return false;
+            }
+            return nclusters >= 1;
+          },
+          &avail) != cudaSuccess)
+    return false;
   return avail && g_orth_cluster_ok.load(std::memory_order_relaxed) != 0;
 }
 
-// CTAs of the grid-wide kernel's cooperative launch (one-time, thread-safe)
+// CTAs of the grid-wide kernel's cooperative launch (once per device, thread-safe)
 struct OrthSetup {
   cudaError_t err;
   int max_ctas;
 };
-const OrthSetup& orth_setup() {
-  static const OrthSetup s = []() {
-    OrthSetup r{cudaSuccess, 0};
-    int dev = 0, sms = 0, per = 0;
-    r.err = cudaGetDevice(&dev);
-    if (r.err == cudaSuccess) r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (r.err == cudaSuccess)
-      r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, orth_persistent, ORTH_NT, 0);
-    r.max_ctas = sms * per;
-    return r;
-  }();
+PerDevice<OrthSetup> g_orth_setup;
+
+OrthSetup orth_setup() {
+  OrthSetup s{cudaSuccess, 0};
+  cudaError_t e = g_orth_setup.get(
+      [](int dev) {
+        OrthSetup r{cudaSuccess, 0};
+        int sms = 0, per = 0;
+        r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (r.err == cudaSuccess)
+          r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, orth_persistent, ORTH_NT, 0);
+        r.max_ctas = sms * per;
+        return r;
+      },
+      &s);
+  if (e != cudaSuccess) s.err = e;
   return s;
 }
 
@@ -605,7 +617,7 @@ cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaS
     g_orth_cluster_ok.store(0, std::memory_order_relaxed);
   }
   const int G = (rows + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
-  const OrthSetup& setup = orth_setup();
+  const OrthSetup setup = orth_setup();
   RET(setup.err);
   if (G > setup.max_ctas || G > b.orth_max_ctas) return cudaErrorInvalidValue;
   OrthArgs a;

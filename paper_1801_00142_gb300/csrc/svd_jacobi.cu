@@ -235,23 +235,28 @@ __global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
   }
 }
 
-// CTAs of the cooperative launch (one-time, thread-safe initialisation)
+// CTAs of the cooperative launch (once per device, thread-safe)
 struct SvdSetup {
   cudaError_t err;
   int max_ctas;
 };
-const SvdSetup& svd_setup() {
-  static const SvdSetup s = []() {
-    SvdSetup r{cudaSuccess, 0};
-    int dev = 0, sms = 0, per = 0;
-    r.err = cudaGetDevice(&dev);
-    if (r.err == cudaSuccess) r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (r.err == cudaSuccess)
-      r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, svd_persistent, NT, 0);
-    r.max_ctas = sms * (per < 2 ? per : 2);
-    if (r.err == cudaSuccess && r.max_ctas < 1) r.err = cudaErrorLaunchOutOfResources;
-    return r;
-  }();
+PerDevice<SvdSetup> g_svd_setup;
+
+SvdSetup svd_setup() {
+  SvdSetup s{cudaSuccess, 0};
+  cudaError_t e = g_svd_setup.get(
+      [](int dev) {
+        SvdSetup r{cudaSuccess, 0};
+        int sms = 0, per = 0;
+        r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (r.err == cudaSuccess)
+          r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, svd_persistent, NT, 0);
+        r.max_ctas = sms * (per < 2 ? per : 2);
+        if (r.err == cudaSuccess && r.max_ctas < 1) r.err = cudaErrorLaunchOutOfResources;
+        return r;
+      },
+      &s);
+  if (e != cudaSuccess) s.err = e;
   return s;
 }
 
@@ -268,7 +273,7 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
       ncols > buf.max_cols)
     return cudaErrorInvalidValue;
   cudaError_t e;
-  const SvdSetup& setup = svd_setup();
+  const SvdSetup setup = svd_setup();
   if (setup.err != cudaSuccess) return setup.err;
   const int max_ctas = setup.max_ctas;
   SvdArgs a;

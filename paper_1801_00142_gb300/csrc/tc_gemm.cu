@@ -1,14 +1,30 @@
 // tcgen05 / TMA GEMM kernel (see tc_gemm.cuh).
 //
 // CTA tile 128 x 128 (M x N), K-block 64 BF16 = one 128-byte swizzle row;
-// persistent CTAs (one per SM) with the accumulator double-buffered in TMEM.
-// Warp 0: TMA producer (one elected thread); warp 1: MMA issuer (one elected
-// thread, 4 x UMMA_K=16 per K-block and product); warp 2: tensor-memory
-// allocation; warps 4-7: epilogue (tcgen05.ld 32x32b, lane quarter = warp % 4).
+// persistent CTAs (one per SM).  Warp 0: TMA producer (one elected thread);
+// warp 1: MMA issuer (one elected thread, 4 x UMMA_K=16 per K-block and
+// product); warp 2: tensor-memory allocation; warps 4-7: epilogue
+// (tcgen05.ld 32x32b, lane quarter = warp % 4).
+//
+// Accumulation.  The tensor core rounds its FP32 accumulator toward zero, so
+// long accumulation chains in tensor memory shrink every output by a
+// systematic relative bias that grows with the chain (measured: ~1e-5 after
+// 64 K-blocks of positive products).  The leading product x0*y0 of the split
+// planes is therefore accumulated one K-block at a time (four MMAs of exact
+// BF16 products, which the tensor core sums without loss at this length)
+// into a double-buffered "main" accumulator, and the epilogue warps add each
+// K-block's result into FP32 registers with round-to-nearest additions while
+// the MMAs of the next K-block run.  The correction products (x0*y1, x1*y0,
+// ...), about 2^-8 of the leading one and of uncorrelated sign, accumulate
+// over the whole K range in a second, per-tile "corr" accumulator that the
+// epilogue adds once at the end of the tile.  Tensor memory: main buffers at
+// columns [0, 256), corr buffers (double-buffered across tiles) at [256, 512).
+//
 // Every mbarrier wait is bounded: on expiry the CTA records an error in
 // dev_err, drains its own outstanding TMA loads and MMAs (bounded again),
 // frees its tensor memory and returns.
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "tc_gemm.cuh"
 
@@ -18,6 +34,8 @@ constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;       // 16 KB per operand plane and stage
 constexpr int NTHREADS = 256;
 constexpr long long WAIT_LIMIT = 1LL << 24;
+constexpr int TMEM_COLS = 4 * BN;     // main [0, 2 BN), corr [2 BN, 4 BN)
+constexpr int CORR_COL = 2 * BN;
 
 struct KParams {
   int M, N, K, batch, splitk, kb_total, kb_per;
@@ -25,6 +43,7 @@ struct KParams {
   int prod_a[6], prod_b[6];
   int a_batched, b_batched;
   int stages;
+  int chunk_kb;   // K-blocks per main accumulation chunk
   TcOutput out;
   int* err;
 };
@@ -223,9 +242,10 @@ __device__ __forceinline__ void store_chunk(const TcOutput& o, long long om,
 
 // Persistent kernel: every CTA walks the output tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ... (tile order: n fastest, then m, then batch x
-// split).  The accumulator is double-buffered in tensor memory (2 x 128
-// columns), so the epilogue of one tile overlaps the main loop of the next;
-// the operand stage ring continues across tiles.
+// split).  The main accumulator is double-buffered per chunk of chunk_kb
+// K-blocks and the corr accumulator per tile, so the MMAs of the next chunk
+// (and of the next tile) run while the epilogue drains and stores; the
+// operand stage ring continues across tiles.
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const KParams p) {
@@ -236,15 +256,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int stage_bytes = (p.pa_planes + p.pb_planes) * TILE_BYTES;
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
   uint64_t* empty = full + S;
-  uint64_t* acc_full = empty + S;     // [2]
-  uint64_t* acc_empty = acc_full + 2; // [2]
-  uint64_t* done = acc_empty + 2;
+  uint64_t* main_full = empty + S;      // [2] per chunk
+  uint64_t* main_empty = main_full + 2; // [2]
+  uint64_t* corr_full = main_empty + 2; // [2] per tile
+  uint64_t* corr_empty = corr_full + 2; // [2]
+  uint64_t* done = corr_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   long long* col_off_all = (long long*)(tmem_slot + 2);   // [4][BN] per-warp column offsets
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int tiles_n = (p.N + BN - 1) / BN, tiles_m = (p.M + BM - 1) / BM;
   const int tiles = tiles_n * tiles_m * p.batch * p.splitk;
+  const int CK = p.chunk_kb;
+  const bool has_corr = p.nprod > 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -252,8 +276,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&main_full[b], 1);
+      mbar_init(&main_empty[b], 4);
+      mbar_init(&corr_full[b], 1);
+      mbar_init(&corr_empty[b], 4);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -261,7 +287,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(2 * BN)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -299,39 +325,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16_128x128();
-    long long g = 0;
-    int j = 0;   // tiles of this CTA
+    long long g = 0;   // k-blocks consumed (stage ring position)
+    long long h = 0;   // main chunks issued
+    int j = 0;         // tiles of this CTA
     bool ok = true;
     for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++j) {
       const int z = t / (tiles_n * tiles_m);
       const int split = z % p.splitk;
       const int kb_begin = split * p.kb_per;
       const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
-      const int buf = j & 1;
-      if (j >= 2) ok = mbar_wait(&acc_empty[buf], (uint32_t)(((j >> 1) - 1) & 1), p.err);
+      const int cb = j & 1;
+      if (has_corr && j >= 2) ok = mbar_wait(&corr_empty[cb], (uint32_t)(((j >> 1) - 1) & 1), p.err);
       if (!ok) break;
-      fence_after();
-      const uint32_t dcol = tmem + (uint32_t)(buf * BN);
+      const uint32_t ccol = tmem + (uint32_t)(CORR_COL + cb * BN);
       for (int kb = kb_begin; kb < kb_end && ok; ++kb, ++g) {
+        const int ci = (kb - kb_begin) % CK;   // position inside the main chunk
+        const int mb = (int)(h & 1);
+        if (ci == 0 && h >= 2) ok = mbar_wait(&main_empty[mb], (uint32_t)(((h >> 1) - 1) & 1), p.err);
+        if (!ok) break;
         const int s = (int)(g % S);
         ok = mbar_wait(&full[s], (uint32_t)((g / S) & 1), p.err);
         if (!ok) break;
         fence_after();
         const uint32_t base = smem_u32(smem + s * stage_bytes);
+        const uint32_t mcol = tmem + (uint32_t)(mb * BN);
         for (int pr = 0; pr < p.nprod; ++pr) {
           const uint32_t a_addr = base + p.prod_a[pr] * TILE_BYTES;
           const uint32_t b_addr = base + (p.pa_planes + p.prod_b[pr]) * TILE_BYTES;
+          const uint32_t dcol = pr == 0 ? mcol : ccol;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             // advance 16 BF16 = 32 B along K inside the swizzled 128-B row
             uint64_t da = smem_desc(a_addr) + (uint64_t)(kk * 2);
             uint64_t db = smem_desc(b_addr) + (uint64_t)(kk * 2);
-            mma_bf16(dcol, da, db, idesc, (kb > kb_begin || pr > 0 || kk > 0) ? 1u : 0u);
+            const bool acc = pr == 0 ? (ci > 0 || kk > 0) : (kb > kb_begin || pr > 1 || kk > 0);
+            mma_bf16(dcol, da, db, idesc, acc ? 1u : 0u);
+          }
+          if (pr == 0 && (ci == CK - 1 || kb == kb_end - 1)) {
+            // the chunk's leading products are issued: the epilogue may take it
+            mma_commit(&main_full[mb]);
+            ++h;
           }
         }
         mma_commit(&empty[s]);
       }
-      if (ok) mma_commit(&acc_full[buf]);
+      // an empty tile (split beyond K) commits nothing it would have to wait for
+      if (ok && has_corr) mma_commit(&corr_full[cb]);
     }
     // the done barrier tracks completion of every MMA issued so far
     mma_commit(done);
@@ -340,14 +379,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp % 4;
     const TcOutput& o = p.out;
     long long* col_off = col_off_all + q * BN;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    long long h = 0;   // main chunks drained
     int j = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++j) {
       const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
       const int bidx = z / p.splitk, split = z % p.splitk;
       const int kb_begin = split * p.kb_per;
       const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
       const int n0 = nt * BN, m0 = mt * BM;
-      const int buf = j & 1;
+      const int cb = j & 1;
       // column offsets of this tile, computed once per warp (the 3-level views
       // need divisions); warp-private, so no barrier across warps is needed
       __syncwarp();
@@ -371,36 +413,63 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const unsigned mp = __ballot_sync(0xffffffffu, paired);
         layouts |= (mc == 0xffffffffu ? 2 : (mp == 0xffffffffu ? 1 : 0)) << (2 * ch);
       }
-      if (!mbar_wait(&acc_full[buf], (uint32_t)((j >> 1) & 1), p.err)) break;
-      fence_after();
+      // accumulate the tile: every main chunk, then the corrections, each
+      // added with round-to-nearest FP32 additions
+      float acc[BN];
+#pragma unroll
+      for (int jj = 0; jj < BN; ++jj) acc[jj] = 0.f;
+      for (int kb = kb_begin; kb < kb_end && ok; kb += CK, ++h) {
+        const int mb = (int)(h & 1);
+        ok = mbar_wait(&main_full[mb], (uint32_t)((h >> 1) & 1), p.err);
+        if (!ok) break;
+        fence_after();
+#pragma unroll
+        for (int c = 0; c < BN; c += 32) {
+          float v[32];
+          tmem_ld32(lane_base + (uint32_t)(mb * BN + c), v);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) acc[c + jj] = __fadd_rn(acc[c + jj], v[jj]);
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&main_empty[mb]))
+                       : "memory");
+      }
+      if (!ok) break;
+      if (has_corr) {
+        ok = mbar_wait(&corr_full[cb], (uint32_t)((j >> 1) & 1), p.err);
+        if (!ok) break;
+        fence_after();
+        if (kb_end > kb_begin) {
+#pragma unroll
+          for (int c = 0; c < BN; c += 32) {
+            float v[32];
+            tmem_ld32(lane_base + (uint32_t)(CORR_COL + cb * BN + c), v);
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) acc[c + jj] = __fadd_rn(acc[c + jj], v[jj]);
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&corr_empty[cb]))
+                       : "memory");
+      }
       const int m = m0 + q * 32 + lane;
-      const bool row_ok = m < p.M;
-      long long om = 0;
+      if (m >= p.M) continue;
       float* dstp = nullptr;
+      long long om = 0;
       if (o.mode == TC_OUT_PARTIAL)
-        dstp = o.f32 + (((long long)split * p.batch + bidx) * p.M + (row_ok ? m : 0)) * (long long)p.N;
-      else if (row_ok)
+        dstp = o.f32 + (((long long)split * p.batch + bidx) * p.M + m) * (long long)p.N;
+      else
         om = bidx * o.scb + idx_off(o.cm, m);
       const float alpha = (float)o.alpha;
-      for (int c = 0; c < BN; c += 32) {
-        float v[32];
-        if (kb_end > kb_begin) {
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), v);
-        } else {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) v[jj] = 0.f;
-        }
-        if (c == BN - 32) {
-          // every TMEM load of this warp is complete: hand the buffer back
-          fence_before();
-          __syncwarp();
-          if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf]))
-                         : "memory");
-        }
-        if (!row_ok) continue;
+      for (int c = 0; c < BN; c += 32) {
         const int ncols = min(32, p.N - (n0 + c));
         if (ncols <= 0) continue;
+        float* v = acc + c;
         if (o.mode == TC_OUT_PARTIAL) {
           float* d = dstp + n0 + c;
           if (ncols == 32 && ((uintptr_t)d & 15) == 0) {
@@ -428,7 +497,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) mbar_wait(done, 0, p.err);
     __syncwarp();
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
                  : "memory");
   }
 }
@@ -453,23 +523,39 @@ EncodeFn get_encode() {
   return fn;
 }
 
-// the kernel's shared-memory opt-in and the SM count of the current device
+// the kernel's shared-memory opt-in and the SM count, once per device
 struct LaunchSetup {
   cudaError_t err;
   int sms;
 };
-const LaunchSetup& launch_setup() {
-  static const LaunchSetup s = []() {
-    LaunchSetup r{cudaSuccess, 0};
-    int dev = 0;
-    r.err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024);
-    if (r.err == cudaSuccess) r.err = cudaGetDevice(&dev);
-    if (r.err == cudaSuccess)
-      r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
-    return r;
+PerDevice<LaunchSetup> g_launch_setup;
+
+cudaError_t launch_setup(int* sms) {
+  LaunchSetup s{cudaSuccess, 0};
+  cudaError_t e = g_launch_setup.get(
+      [](int dev) {
+        LaunchSetup r{cudaSuccess, 0};
+        r.err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024);
+        if (r.err == cudaSuccess)
+          r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
+        return r;
+      },
+      &s);
+  if (e != cudaSuccess) return e;
+  *sms = s.sms;
+  return s.err;
+}
+
+// K-blocks per main accumulation chunk: XTRG_TC_CHUNK_KB in [1, 64] if set,
+// else 2 (128 terms of exact BF16 products per tensor-memory chain)
+int chunk_kb() {
+  static const int v = []() {
+    const char* e = getenv("XTRG_TC_CHUNK_KB");
+    const int x = e ? atoi(e) : 0;
+    return (x >= 1 && x <= 64) ? x : 2;
   }();
-  return s;
+  return v;
 }
 
 // 4-D map: (k, rows, batch, plane), box (64, 128, 1, 1), 128-byte swizzle,
@@ -523,16 +609,16 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   if (S > 4) S = 4;
   if (S < 2) return cudaErrorInvalidValue;
   p.stages = S;
+  p.chunk_kb = chunk_kb();
   p.out = out;
   p.err = dev_err;
   CUtensorMap ma, mb;
   cudaError_t e;
   if ((e = make_map(&ma, A)) != cudaSuccess) return e;
   if ((e = make_map(&mb, B)) != cudaSuccess) return e;
-  const int smem = S * stage_bytes + 1024 + (2 * S + 5) * 8 + 8 + 4 * BN * 8 + 64;
-  const LaunchSetup& setup = launch_setup();
-  if (setup.err != cudaSuccess) return setup.err;
-  const int sms = setup.sms;
+  const int smem = S * stage_bytes + 1024 + (2 * S + 9) * 8 + 8 + 4 * BN * 8 + 64;
+  int sms = 0;
+  if ((e = launch_setup(&sms)) != cudaSuccess) return e;
   const long long tiles =
       (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * (long long)batch * splitk;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;

@@ -34,6 +34,7 @@
 #include "mixed_ops.cuh"
 #include "subspace_split.cuh"
 #include "tc_gemm.cuh"
+#include "tc_gemm_entry.cuh"
 
 namespace {
 
@@ -1109,12 +1110,11 @@ extern "C" xtrg_status xtrg_set_profiling(xtrg_ctx* ctx, int on) {
   return XTRG_OK;
 }
 
-namespace {
-struct TcWs {
-  size_t a, b, part, total;
-};
-TcWs tc_ws(int M, int N, int K, int batch, int planes, int splitk) {
-  TcWs w;
+// Layout of the scratch of one FP64 tensor-core GEMM call (shared by the
+// workspace and the static-scratch entry points): A planes, B planes, split-K
+// partials, error flag.
+TcGemmScratch tc_gemm_scratch(int M, int N, int K, int batch, int planes, int splitk) {
+  TcGemmScratch w;
   const size_t ld = (size_t)tc_ld(K);
   w.a = up((size_t)planes * batch * M * ld * 2);
   w.b = up((size_t)planes * batch * N * ld * 2);
@@ -1122,25 +1122,19 @@ TcWs tc_ws(int M, int N, int K, int batch, int planes, int splitk) {
   w.total = w.a + w.b + w.part + ALIGN;
   return w;
 }
-}  // namespace
 
-extern "C" size_t xtrg_tc_gemm_workspace_bytes(int M, int N, int K, int batch, int planes,
-                                               int splitk) {
-  if (M < 1 || N < 1 || K < 1 || batch < 1 || planes < 1 || planes > 3 || splitk < 1) return 0;
-  return tc_ws(M, N, K, batch, planes, splitk).total;
-}
-
-extern "C" xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int N,
-                                    int K, int batch, int planes, int nprod, int splitk,
-                                    void* workspace, size_t bytes, void* stream) {
-  if (!A || !B || !C || !workspace || ((uintptr_t)workspace % ALIGN) != 0) return XTRG_EINVAL;
+xtrg_status tc_gemm_check_args(const double* A, const double* B, double* C, int M, int N, int K,
+                               int batch, int planes, int nprod, int splitk) {
+  if (!A || !B || !C) return XTRG_EINVAL;
   if (M < 1 || N < 1 || K < 1 || batch < 1 || planes < 2 || planes > 3 || splitk < 1)
     return XTRG_EINVAL;
   if (!(nprod == 1 || nprod == 3 || (nprod == 6 && planes == 3))) return XTRG_EINVAL;
-  const TcWs w = tc_ws(M, N, K, batch, planes, splitk);
-  if (bytes < w.total) return XTRG_ENOMEM;
-  cudaStream_t st = (cudaStream_t)stream;
-  char* base = (char*)workspace;
+  return XTRG_OK;
+}
+
+xtrg_status tc_gemm_run(const double* A, const double* B, double* C, int M, int N, int K, int batch,
+                        int planes, int nprod, int splitk, char* base, cudaStream_t st) {
+  const TcGemmScratch w = tc_gemm_scratch(M, N, K, batch, planes, splitk);
   __nv_bfloat16* pa = (__nv_bfloat16*)base;
   __nv_bfloat16* pb = (__nv_bfloat16*)(base + w.a);
   float* part = (float*)(base + w.a + w.b);
@@ -1170,6 +1164,22 @@ extern "C" xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C,
     return XTRG_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return XTRG_ECUDA;
   return h ? XTRG_ETIMEOUT : XTRG_OK;
+}
+
+extern "C" size_t xtrg_tc_gemm_workspace_bytes(int M, int N, int K, int batch, int planes,
+                                               int splitk) {
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || planes < 1 || planes > 3 || splitk < 1) return 0;
+  return tc_gemm_scratch(M, N, K, batch, planes, splitk).total;
+}
+
+extern "C" xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int N,
+                                    int K, int batch, int planes, int nprod, int splitk,
+                                    void* workspace, size_t bytes, void* stream) {
+  TRY(tc_gemm_check_args(A, B, C, M, N, K, batch, planes, nprod, splitk));
+  if (!workspace || ((uintptr_t)workspace % ALIGN) != 0) return XTRG_EINVAL;
+  if (bytes < tc_gemm_scratch(M, N, K, batch, planes, splitk).total) return XTRG_ENOMEM;
+  return tc_gemm_run(A, B, C, M, N, K, batch, planes, nprod, splitk, (char*)workspace,
+                     (cudaStream_t)stream);
 }
 
 const char* xtrg_batch_last_error();   // batch.cu

@@ -54,3 +54,35 @@ def test_tc_gemm_matches_fp64(torch_lib, M, N, K, batch, planes, nprod, splitk):
     lib.xtrg_tc_gemm(dA.data_ptr(), dB.data_ptr(), dC.data_ptr(), M, N, K, batch, planes, nprod,
                      splitk, p, nbytes, torch.cuda.current_stream().cuda_stream)
     assert np.array_equal(dC.cpu().numpy(), C)
+
+
+@pytest.mark.parametrize("exact_bf16,planes,nprod", [(True, 2, 1), (False, 3, 6)])
+def test_tc_gemm_long_chains_are_unbiased(torch_lib, exact_bf16, planes, nprod):
+    """Long accumulations on one tile (K = 65536, no split-K) of positive
+    products.  The tensor core's accumulator rounds toward zero, so chaining
+    every K-block in tensor memory shrank such sums by ~4e-4 relative; the
+    kernel keeps the leading products' chains to a few K-blocks and sums them
+    in round-to-nearest FP32, so the mean signed error must stay at rounding
+    level while the rms error is bounded by round-to-nearest accumulation."""
+    torch, lib = torch_lib
+    M = N = 128
+    K = 65536
+    rng = np.random.default_rng(20260)
+    A = rng.uniform(0.5, 1.0, (1, M, K))
+    B = rng.uniform(0.5, 1.0, (1, N, K))
+    if exact_bf16:
+        A = torch.from_numpy(A).to(torch.bfloat16).to(torch.float64).numpy()
+        B = torch.from_numpy(B).to(torch.bfloat16).to(torch.float64).numpy()
+    ref = np.einsum("bmk,bnk->bmn", A, B)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    dC = torch.zeros((1, M, N), dtype=torch.float64, device="cuda")
+    nbytes = lib.xtrg_tc_gemm_workspace_bytes(M, N, K, 1, planes, 1)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    p = (ws.data_ptr() + 255) // 256 * 256
+    lib.xtrg_tc_gemm(dA.data_ptr(), dB.data_ptr(), dC.data_ptr(), M, N, K, 1, planes, nprod, 1,
+                     p, nbytes, torch.cuda.current_stream().cuda_stream)
+    rel = (dC.cpu().numpy() - ref) / ref
+    print("bias", rel.mean(), "rms", np.sqrt((rel ** 2).mean()))
+    assert abs(rel.mean()) <= 3e-8
+    assert np.sqrt((rel ** 2).mean()) <= 1e-6

@@ -4,6 +4,11 @@ Calls only ``oracle`` (and the shared ``workloads`` descriptions); no value
 here comes from the CUDA path.  Run from the repository root:
 
     python tests/golden/make_golden.py [name ...]
+    python tests/golden/make_golden.py --long xx_L32_D256
+
+``--long`` runs one of the long FP64 reference schedules row by row and
+rewrites its file after every doubling (hours of CPU at D* = 256; no
+perturbation sensitivity is computed for these).
 """
 import json
 import os
@@ -62,6 +67,33 @@ def run(w):
             "truncated": truncated}
 
 
+def run_long(w, path):
+    """Init, then the doublings one at a time, writing the rows so far after
+    each (so a long run can be followed and is not lost if interrupted)."""
+    H = hamiltonian(w)
+    t0 = time.time()
+    rho, lnc = xo.init_rho(H, w.tau0, w.order, w.dstar, _init_sweeps(w), w.svd_rel_tol)
+    beta = w.tau0
+    rows = []
+    for n in range(w.n_doublings + 1):
+        if n > 0:
+            st = xo.CompressStats()
+            rho, lnc = xo.double(rho, lnc, w.dstar, w.sweeps, w.svd_rel_tol, st)
+            beta *= 2.0
+        row = xo.observables(H, rho, lnc, beta, w.L)
+        row["bond_dims"] = [x.shape[3] for x in rho[:-1]]
+        if n > 0:
+            row["trunc"] = st.max_discarded
+        row["elapsed_s"] = time.time() - t0
+        rows.append(row)
+        with open(path + ".tmp", "w") as f:
+            json.dump({"workload": w.__dict__, "rows": rows, "oracle_seconds": time.time() - t0,
+                       "truncated": any(r.get("trunc", 0.0) > 1e-24 for r in rows),
+                       "complete": n == w.n_doublings}, f, indent=1)
+        os.replace(path + ".tmp", path)
+        print(w.name, f"beta={beta:g}", f"{time.time() - t0:.0f}s", flush=True)
+
+
 def main(names):
     cases = {w.name: w for w in wl.small_cases() + [wl.CHAIN_L8] + wl.small_lattice_cases()}
     for name in names or list(cases):
@@ -71,5 +103,11 @@ def main(names):
         print(name, f"{out['oracle_seconds']:.1f}s")
 
 
+LONG = {w.name: w for w in (wl.CHAIN_L32_XX, wl.CHAIN_L64_XX)}
+
 if __name__ == "__main__":
-    main(sys.argv[1:])
+    if sys.argv[1:2] == ["--long"]:
+        for name in sys.argv[2:]:
+            run_long(LONG[name], os.path.join(HERE, f"oracle_{name}.json"))
+    else:
+        main(sys.argv[1:])

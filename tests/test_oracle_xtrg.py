@@ -204,3 +204,31 @@ def test_planted_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(xo, "left_part", good)
     rho_good, lnc_good = xo.init_rho(H2, 2 ** -4, 4, 256, 4, 1e-15)
     assert np.abs(np.exp(lnc) * dense(rho) - np.exp(lnc_good) * dense(rho_good)).max() > 1e-6
+
+
+def test_transfer_traces_match_dense_on_a_nonsymmetric_mpo():
+    """The transfer-matrix traces of the oracle against the dense operator of
+    a random, non-symmetric MPO (so Tr(R R) differs from ||R||_F^2 and from
+    Tr(R^T R)): a contraction of Tr(rho rho) that paired the physical indices
+    like the Frobenius norm, or a trace that summed the wrong pair, fails."""
+    rng = np.random.default_rng(11)
+    dims = [1, 3, 5, 4, 1]
+    W = [rng.standard_normal((dims[i], 2, 2, dims[i + 1])) for i in range(4)]
+    R = hm.mpo_to_dense(W)
+    assert np.abs(R - R.T).max() > 1e-2            # genuinely non-symmetric
+    assert abs(xo.trace(W) - np.trace(R)) < 1e-12 * np.abs(R).sum()
+    assert abs(xo.frobenius2(W) - np.sum(R * R)) < 1e-12 * np.sum(R * R)
+    assert abs(xo.trace_rho_rho(W) - np.trace(R @ R)) < 1e-12 * np.sum(R * R)
+    H = hm.xxz_chain_mpo(4, 1.0, 0.6)
+    Hd = hm.mpo_to_dense(H)
+    assert abs(xo.trace_H_rho(H, W) - np.trace(Hd @ R)) < 1e-12 * np.abs(Hd).sum() * np.abs(R).max()
+    assert abs(xo.trace_H2_rho(H, W) - np.trace(Hd @ Hd @ R)) < 1e-11 * np.sum(Hd * Hd) * np.abs(R).max() * 16
+    # the Hermiticity defect of observables() is ||R - R^T||_F / ||R||_F
+    o = xo.observables(H, W, 0.0, 1.0, 4)
+    want = np.linalg.norm(R - R.T) / np.linalg.norm(R)
+    assert abs(o["herm"] - want) < 1e-10
+    # and it vanishes for a symmetrised MPO (R + R^T as a direct sum)
+    WT = [w.transpose(0, 2, 1, 3) for w in W]
+    S = xo.direct_sum(W, 1.0, WT)
+    assert np.abs(hm.mpo_to_dense(S) - (R + R.T)).max() < 1e-12 * np.abs(R).max() * 8
+    assert xo.observables(H, S, 0.0, 1.0, 4)["herm"] < 1e-7

@@ -65,6 +65,10 @@ CHAIN_L64_XX = ChainWorkload(name="xx_L64_D256", L=64, Delta=0.0,
                              tau0=2.0 ** -12, dstar=256, sweeps=4, n_doublings=18)
 CHAIN_L64_XXX = ChainWorkload(name="xxx_L64_D256", L=64, Delta=1.0,
                               tau0=2.0 ** -12, dstar=256, sweeps=4, n_doublings=18)
+# The same schedule on a 32-site XX chain: the FP64 reference of the
+# mixed-precision accuracy gate at a length the oracle finishes in hours.
+CHAIN_L32_XX = ChainWorkload(name="xx_L32_D256", L=32, Delta=0.0,
+                             tau0=2.0 ** -12, dstar=256, sweeps=4, n_doublings=18)
 
 
 def batched_instances(n: int = 64, seed: int = 180100142, n_grids: int = 8,

@@ -1,12 +1,16 @@
 """Benchmark: XTRG beta-doubling steps on one GB300 (or N replicas).
 
-A step is one doubling rho <- compress(rho^T rho) of the 64-site Heisenberg
-chain at D* = 256 with 4 full sweeps, followed by the trace and the
-thermodynamic observables (the whole hot path after initialisation).  Steps
-are timed once the bonds have saturated at D*.  Prints one JSON line.
+A step is one doubling rho <- compress(rho^T rho) of the 64-site XX chain at
+D* = 256 with 4 full sweeps, followed by the trace and the thermodynamic
+observables (the whole hot path after initialisation).  The timed steps are
+the saturated doublings of the schedule tau0 = 2^-12 -> beta = 64, repeated
+from a device checkpoint when more steps are asked for than the schedule
+has.  Prints one JSON line with the accuracy of the run against the XX
+chain's closed form, the FP64 GPU path on the same state, the roofline of
+the tensor-core GEMM and the CPU oracle.
 
   python bench.py [--steps K] [--warmup W] [--prec bf16x6|bf16x3|fp64]
-                  [--impl native|reference] [--fp64-sample]
+                  [--impl native|reference] [--no-fp64-arm] [--no-cpu-baseline]
 
 Multi-GPU (torchrun, one rank per GPU): every rank runs an independent
 replica (the doubling of one instance does not shard); value is the sum of
@@ -34,9 +38,12 @@ import workloads as wl  # noqa: E402
 METRIC = ("XTRG doubling steps/s & TFLOP/s @D*=256,L=64: mixed vs FP64, "
           "|Δf|/site≤1e-6")
 UNIT = "doubling steps/s"
-W = wl.CHAIN_L64_XXX
-DESC = ("Heisenberg XXX chain, L=64 open, J=1, Delta=1, D*=256, 4 sweeps/doubling, "
-        "tau0=2^-12 doubled to beta=64; the last steps of that schedule are timed")
+W = wl.CHAIN_L64_XX
+# doublings that start below this beta run in FP64 (the precision schedule
+# under which the tensor-core path meets |df|/site <= 1e-6)
+BETA_SWITCH = 0.25
+DESC = ("Heisenberg XX chain (XXZ, Delta=0), L=64 open, J=1, D*=256, 4 sweeps/doubling, "
+        "tau0=2^-12 doubled to beta=64; the saturated doublings of that schedule are timed")
 L2_NOTE = ("no flush: every update streams operands far larger than L2 (one environment "
            "~100 MB, one resident half ~400 MB per plane set; ~75 GB working set)")
 
@@ -48,7 +55,7 @@ def set_workload(L, dstar):
     global W, DESC
     if (L, dstar) != (W.L, W.dstar):
         W = W.with_(name=f"xxx_L{L}_D{dstar}", L=L, dstar=dstar)
-        DESC = (f"Heisenberg XXX chain, L={L} open, J=1, Delta=1, D*={dstar}, 4 sweeps/doubling, "
+        DESC = (f"Heisenberg XX chain, L={L} open, J=1, Delta=0, D*={dstar}, 4 sweeps/doubling, "
                 f"tau0=2^-12 doubled to beta=64 (profiling case)")
 
 
@@ -154,8 +161,6 @@ def run_reference(args):
     if rank != 0:
         return
     oracle_update_seconds(1)          # warm-up of BLAS threads
-    for _ in range(max(0, args.warmup - 1)):
-        pass
     times = []
     for _ in range(args.steps):
         times.append(oracle_update_seconds(1, seed=len(times) + 1))
@@ -166,8 +171,12 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": t * updates * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": DESC, "L": W.L, "dstar": W.dstar, "sweeps": W.sweeps,
-                      "tau0": W.tau0, "prec": "fp64 (oracle)", "l2": L2_NOTE,
+           "config": {"workload": DESC, "L": W.L, "Delta": W.Delta, "dstar": W.dstar,
+                      "sweeps": W.sweeps, "tau0": W.tau0, "prec": "fp64 (oracle)",
+                      "beta_switch": BETA_SWITCH, "l2": L2_NOTE,
+                      "timed_window": ("per step: one oracle two-site update at the saturated "
+                                       "bond 256 of the doubling (C_E, SVD split, environment "
+                                       "update), scaled by the doubling's updates"),
                       "parallelism": "rank 0 only"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                             "sample": f"one oracle two-site update per step at bond 256, median "
@@ -192,9 +201,44 @@ def aggregate(ms_local, steps_local, dist=None, device=None):
 
 
 # ---------------------------------------------------------------- GPU path
+def free_fermion_f(L, beta, J=1.0):
+    """Free energy per site of the open XX chain (Delta = 0) in closed form:
+    Jordan-Wigner fermions with eps_k = J cos(k pi / (L+1)),
+    ln Z = sum_k ln(1 + e^{-beta eps_k}) (App. F of the paper).  Used only to
+    state the accuracy of the timed run next to its throughput."""
+    k = np.arange(1, L + 1)
+    eps = J * np.cos(k * np.pi / (L + 1))
+    lnZ = float(np.sum(np.logaddexp(0.0, -beta * eps)))
+    return -lnZ / (L * beta)
+
+
+def traffic_from_profile(kernel_src):
+    """DRAM bytes per C_E launch of tc_gemm_kernel from the committed ncu
+    summary, if that summary was taken of the current kernel source (its
+    sha256 is recorded in the summary); otherwise None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_tc_gemm_ce_L64_D256_bf16x6.md")
+    try:
+        text = open(path).read()
+        src = open(kernel_src, "rb").read()
+    except OSError:
+        return None, None
+    sha = hashlib.sha256(src).hexdigest()
+    fields = {}
+    for ln in text.splitlines():
+        key, sep, val = ln.partition(":")
+        if sep and key.strip() in ("source_sha256", "traffic_bytes_per_launch", "launch_shape"):
+            fields[key.strip()] = val.strip().strip("`")
+    if fields.get("source_sha256") != sha:
+        return None, "ncu summary is of another kernel source"
+    try:
+        return float(fields["traffic_bytes_per_launch"]), fields.get("launch_shape")
+    except (KeyError, ValueError):
+        return None, None
+
+
 def run_native(args):
     import torch
-    from paper_1801_00142_gb300 import _lib
     from paper_1801_00142_gb300.engine import XTRG
 
     ws, rank, local = dist_env()
@@ -205,21 +249,42 @@ def run_native(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    beta_end = W.betas[-1]
+    xx = W.Delta == 0.0
 
     eng = XTRG.xxz(W.L, W.J, W.Delta, tau0=W.tau0, dstar=W.dstar, sweeps=W.sweeps,
-                   order=W.order, prec=args.prec, beta_switch=0.0, device=str(dev))
+                   order=W.order, prec=args.prec, beta_switch=BETA_SWITCH, device=str(dev))
     st = eng.stream
+    # set-up: initialisation and the doublings up to the first state that the
+    # timed doublings start from (mixed arithmetic, bonds saturated at D*)
     eng.init()
-    # the full schedule tau0 -> 2^n_doublings tau0; the last W + K doublings
-    # are the warm-up and the timed steps, the ones before them are set-up
-    n_setup = max(0, W.n_doublings - args.warmup - args.steps)
-    for _ in range(n_setup + args.warmup):
+    rows_sched = [eng.observables()]
+    while True:
+        o = rows_sched[-1]
+        if o["max_bond"] == W.dstar and (args.prec == "fp64" or o["beta"] >= BETA_SWITCH):
+            break
+        if o["beta"] >= beta_end:
+            raise RuntimeError("bonds did not saturate inside the schedule")
         eng.double()
-        eng.observables()
-    assert eng.observables()["max_bond"] == W.dstar
+        rows_sched.append(eng.observables())
+    beta0 = rows_sched[-1]["beta"]
+    ckpt = eng.checkpoint()
 
+    cur = {"beta": beta0}
+
+    def step():
+        # the timed doublings walk beta0 -> beta_end and start over from the
+        # checkpoint, so every timed step is a saturated doubling of the schedule
+        if cur["beta"] >= beta_end:
+            eng.restore(ckpt)
+        eng.double()
+        o = eng.observables()
+        cur["beta"] = o["beta"]
+        return o
+
+    for _ in range(args.warmup):
+        rows_sched.append(step())
     clocks = ClockSampler(local)
-    eng.set_profiling(True)
     s0 = eng.counters()
     if dist:
         dist.barrier()
@@ -232,8 +297,7 @@ def run_native(args):
     e0.record(st)
     rows = []
     for _ in range(args.steps):
-        eng.double()
-        rows.append(eng.observables())
+        rows.append(step())
     e1.record(st)
     torch.cuda.synchronize(dev)
     if args.ncu_region:
@@ -242,17 +306,34 @@ def run_native(args):
         dist.barrier()
     clk = clocks.stop()
     s1 = eng.counters()
-    eng.set_profiling(False)
     ms, steps_total, value = aggregate(e0.elapsed_time(e1), args.steps, dist, dev)
+    timed_betas = sorted({r["beta"] for r in rows})
 
-    # end to end through the C ABI with host buffers: upload rho, double,
-    # observables, download rho, every step
-    sites, lnc, beta = eng.get_state()
-    h2d = sum(w.nbytes for w in sites)
+    # profiled pass over the same doublings (beta0 -> beta_end): every
+    # tensor-core GEMM launch and truncation bracketed by CUDA events on the
+    # context's stream; kept out of the timed region above
+    eng.restore(ckpt)
+    cur["beta"] = beta0
+    eng.set_profiling(True)
+    p0 = eng.counters()
+    n_cycle = int(round(math.log2(beta_end / beta0)))
+    for _ in range(n_cycle):
+        step()
+    p1 = eng.counters()
+    eng.set_profiling(False)
+
+    # end to end through the C ABI with host buffers, over the same doublings:
+    # upload rho, double, observables, download rho, every step
+    eng.restore(ckpt)
+    host0 = eng.get_state()
+    sites, lnc, beta = host0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    d2h = 0
+    h2d = d2h = 0
     for _ in range(max(1, args.steps)):
+        if beta >= beta_end:
+            sites, lnc, beta = host0
+        h2d = sum(w.nbytes for w in sites)
         eng.set_state(sites, lnc, beta, right_canonical=True)
         eng.double()
         eng.observables()
@@ -261,36 +342,62 @@ def run_native(args):
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps)
 
+    fp64 = None
+    if args.prec != "fp64" and not args.no_fp64_arm and rank == 0:
+        fp64 = fp64_arm(XTRG, host0, dev)
+    eng.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     peaks, src = measured_peaks()
     nprod = {"bf16x6": 6, "bf16x3": 3}.get(args.prec, 0)
-    tc_ms = s1["tc_ms"] - s0["tc_ms"]
-    tc_fl = s1["tc_flops"] - s0["tc_flops"]
+    tc_ms = p1["tc_ms"] - p0["tc_ms"]
+    tc_fl = p1["tc_flops"] - p0["tc_flops"]
+    tc_n = p1["tc_launches"] - p0["tc_launches"]
     contr = s1["contraction_flops"] - s0["contraction_flops"]
     tc_tflops = tc_fl / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
     roof = None
     if nprod:
         bf16_peak = peaks["bf16_tflops_sustained"]
         peak = bf16_peak / nprod
+        traffic, shape = traffic_from_profile(
+            os.path.join(ROOT, "paper_1801_00142_gb300", "csrc", "tc_gemm.cu"))
         roof = {"bound": "tensor", "achieved": tc_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": (tc_tflops / peak) if tc_tflops else None, "traffic": None,
+                "frac": (tc_tflops / peak) if tc_tflops else None, "traffic": traffic,
+                "traffic_note": shape,
                 "kernel": "tc_gemm_kernel (tcgen05 BF16 split-plane GEMM)",
                 "peak_note": (f"{src} bf16 sustained {bf16_peak} TFLOP/s / {nprod} BF16 products per "
-                              f"algorithmic FP32-class multiply-add; issued "
-                              f"{tc_tflops * nprod if tc_tflops else None:.1f} TFLOP/s"),
-                "launches": s1["tc_launches"] - s0["tc_launches"],
-                "avg_launch_ms": tc_ms / max(1, s1["tc_launches"] - s0["tc_launches"])}
+                              f"algorithmic FP32-class multiply-add (of measured); issued "
+                              f"{tc_tflops * nprod if tc_tflops else 0:.1f} TFLOP/s"),
+                "timing": (f"CUDA events around each of the {tc_n} launches of a profiled pass "
+                           f"over the timed doublings (beta {beta0:g} -> {beta_end:g})"),
+                "launches": tc_n, "avg_launch_ms": tc_ms / max(1, tc_n)}
+    df_sched = [abs(r["f"] - free_fermion_f(W.L, r["beta"], W.J)) for r in rows_sched] if xx else []
+    df_timed = [abs(r["f"] - free_fermion_f(W.L, r["beta"], W.J)) for r in rows] if xx else []
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-           "config": {"workload": DESC, "L": W.L, "dstar": W.dstar, "sweeps": W.sweeps,
-                      "tau0": W.tau0, "prec": args.prec,
-                      "beta": [rows[0]["beta"], rows[-1]["beta"]],
+           "config": {"workload": DESC, "L": W.L, "Delta": W.Delta, "dstar": W.dstar,
+                      "sweeps": W.sweeps, "tau0": W.tau0, "prec": args.prec,
+                      "beta_switch": BETA_SWITCH,
+                      "timed_betas": [timed_betas[0], timed_betas[-1]],
+                      "timed_window": (f"doublings beta {beta0:g} -> {beta_end:g} of the schedule "
+                                       f"(bonds saturated at D*), restarted from a device "
+                                       f"checkpoint at beta {beta0:g} after beta {beta_end:g}"),
                       "l2": L2_NOTE,
                       "parallelism": f"replicas x{ws}"},
+           "accuracy": ({"vs_exact_max_abs_df_per_site_setup": max(df_sched),
+                         "vs_exact_max_abs_df_per_site_timed": max(df_timed),
+                         "exact": "free-fermion closed form of the XX chain",
+                         "vs_fp64_one_doubling_abs_df_per_site":
+                             fp64.get("mixed_vs_fp64_abs_df") if fp64 else None,
+                         "gate": "|df|/site <= 1e-6 against the FP64 path at the same D*",
+                         "note": ("the exact result differs from XTRG at D*=256 by the "
+                                  "truncation error both paths share; the FP64 comparison is "
+                                  "one doubling of both paths from the same state")}
+                        if xx else None),
            "tflops": contr / (ms / 1e3) / 1e12 * ws,
            "tflops_note": "algorithmic 2MNK of the contraction GEMMs per second (whole job)",
            "roofline": roof,
@@ -299,14 +406,109 @@ def run_native(args):
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": s1["kernel_launches"] - s0["kernel_launches"],
            "exact_split_fallbacks": s1["exact_split_fallbacks"] - s0["exact_split_fallbacks"],
-           "truncation_ms_per_step": (s1["split_ms"] - s0["split_ms"]) / args.steps,
+           "truncation_ms_per_step": (p1["split_ms"] - p0["split_ms"]) / n_cycle,
+           "tc_gemm_ms_per_step": tc_ms / n_cycle,
            "orth_cluster_calls": s1["orth_cluster_calls"] - s0["orth_cluster_calls"],
+           "orth_fallbacks": s1["orth_fallbacks"] - s0["orth_fallbacks"],
+           "fp64_arm": fp64,
            "observables_last": {k: rows[-1][k] for k in ("beta", "lnZ", "f", "u", "max_bond")}}
+    if fp64 and fp64.get("ms_per_step"):
+        out["fp64_ms_per_step"] = fp64["ms_per_step"]
+        out["speedup_vs_fp64"] = fp64["ms_per_step"] / (ms / args.steps)
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(2)
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def fp64_arm(XTRG, host_state, dev):
+    """The FP64 GPU path on the same saturated state: one doubling with one
+    full sweep, every two-site update and the initial environment pass timed
+    by CUDA events inside the library; a 4-sweep doubling is that doubling
+    plus the measured mean update time for the 3 further sweeps.  (A full
+    4-sweep FP64 doubling at D* = 256, L = 64 takes several minutes.)"""
+    import torch
+    sites, lnc, beta = host_state
+    e = XTRG.xxz(W.L, W.J, W.Delta, tau0=W.tau0, dstar=W.dstar, sweeps=1, order=W.order,
+                 prec="fp64", device=str(dev))
+    e.set_state(sites, lnc, beta, right_canonical=True)
+    e.set_profiling(True)
+    c0 = e.counters()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record(e.stream)
+    e.double()
+    e.observables()
+    b.record(e.stream)
+    torch.cuda.synchronize(dev)
+    c1 = e.counters()
+    o64 = e.observables()
+    e.close()
+    t1 = a.elapsed_time(b)
+    # the tensor-core path doubles the same state with the same single sweep
+    m = XTRG.xxz(W.L, W.J, W.Delta, tau0=W.tau0, dstar=W.dstar, sweeps=1, order=W.order,
+                 prec="bf16x6", device=str(dev), keep_parts=False)
+    m.set_state(sites, lnc, beta, right_canonical=True)
+    m.double()
+    om = m.observables()
+    m.close()
+    n_upd = c1["fp64_updates_timed"] - c0["fp64_updates_timed"]
+    upd_ms = (c1["fp64_update_ms"] - c0["fp64_update_ms"]) / max(1, n_upd)
+    extra = (W.sweeps - 1) * 2 * (W.L - 1)
+    return {"ms_per_step": t1 + extra * upd_ms, "measured_ms_1_sweep": t1,
+            "updates_timed": n_upd, "ms_per_update": upd_ms,
+            "env_pass_ms": c1["fp64_env_pass_ms"] - c0["fp64_env_pass_ms"],
+            "beta": beta, "mixed_vs_fp64_abs_df": abs(om["f"] - o64["f"]),
+            "method": (f"one FP64 doubling with 1 sweep from the timed window's start state "
+                       f"(CUDA events), plus {extra} further two-site updates at the measured "
+                       f"mean FP64 update time for the {W.sweeps}-sweep doubling")}
+
+
+def run_gemm_microbench(args):
+    """The tensor-core contraction primitive alone at the C_E shape of a
+    saturated two-site update (M = N = 4 D*, K = D*^2, 3 planes, 6 products,
+    the split-K the engine picks for it), through xtrg_tc_gemm: CUDA events
+    around the GEMM kernel's launches (the plane conversions of the FP64
+    inputs are outside the events).  One JSON line; used for the roofline and
+    for small profiler captures of that launch."""
+    import torch
+    from paper_1801_00142_gb300 import _lib
+    D = W.dstar
+    M = N = 4 * D
+    K = D * D
+    splitk = args.splitk
+    rng = np.random.default_rng(0)
+    A = torch.from_numpy(rng.standard_normal((M, K)) / D).cuda()
+    B = torch.from_numpy(rng.standard_normal((N, K)) / D).cuda()
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    nb = _lib.xtrg_tc_gemm_workspace_bytes(M, N, K, 1, 3, splitk)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    p = (ws.data_ptr() + 255) // 256 * 256
+    st = torch.cuda.current_stream().cuda_stream
+    for _ in range(max(1, args.warmup)):
+        _lib.xtrg_tc_gemm(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1, 3, 6, splitk, p, nb,
+                          st)
+    ts = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        _lib.xtrg_tc_gemm(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1, 3, 6, splitk, p, nb,
+                          st)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    peaks, src = measured_peaks()
+    flops = 2.0 * M * N * K
+    print(json.dumps({"microbench": "tc_gemm C_E", "M": M, "N": N, "K": K, "splitk": splitk,
+                      "planes": 3, "nprod": 6, "ms_median_call": ms,
+                      "algorithmic_tflops_call": flops / ms / 1e9,
+                      "note": "call = plane conversion of A and B + GEMM + FP64 split-K sum",
+                      "peak_bf16_sustained_over_6": peaks["bf16_tflops_sustained"] / 6}))
 
 
 def main():
@@ -317,6 +519,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--microbench", choices=["ce"], default=None,
+                    help="time the tensor-core GEMM alone at the C_E shape of the workload")
+    ap.add_argument("--splitk", type=int, default=7, help="split-K of --microbench ce")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="skip the FP64 GPU comparison arm (several minutes at L=64)")
     ap.add_argument("--ncu-region", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop")
     ap.add_argument("--L", type=int, default=W.L,
@@ -325,7 +532,9 @@ def main():
                     help="bond cap D* (smaller caps only for profiler captures)")
     args = ap.parse_args()
     set_workload(args.L, args.dstar)
-    if args.impl == "reference":
+    if args.microbench:
+        run_gemm_microbench(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)

@@ -97,7 +97,9 @@ typedef struct {
   double c;             /* specific heat per site, beta^2 (<H^2> - <H>^2) / N */
   double lnZ2;          /* ln Z(2 beta) = ln ||rho(beta)||_F^2 (Sec. II B)    */
   double trunc_err;     /* largest discarded weight of the last sweep          */
-  double herm_defect;   /* reserved, 0                                        */
+  double herm_defect;   /* Hermiticity defect ||rho - rho^T||_F / ||rho||_F of the
+                           stored rho (Sec. II B); FP64 transfers, resolved down
+                           to ~1.5e-8 (it is a square root of a difference)     */
   int max_bond;         /* largest bond dimension of the current rho          */
   int n_doublings;      /* doublings done since xtrg_init                     */
 } xtrg_obs;
@@ -128,6 +130,14 @@ xtrg_status xtrg_trace(xtrg_ctx* ctx, double* lnZ);
 /* Thermodynamics of Eq. ThermalQuan at the current beta. */
 xtrg_status xtrg_observables(xtrg_ctx* ctx, xtrg_obs* out);
 
+/* MPO entanglement of the current rho at every bond (Sec. IV A, Eq. purif):
+ * rho is read as a state of the doubled local space |s>|t>, normalised in the
+ * Frobenius norm; at bond i (between sites i-1 and i, i = 1..L-1) its Schmidt
+ * values s_k give p_k = s_k^2 / sum s^2 and S[i-1] = -sum_k p_k ln p_k.
+ * S: host array of n >= L-1 doubles.  FP64 throughout (one Jacobi SVD per
+ * bond on a copy of rho; rho itself is unchanged).  Synchronises the stream. */
+xtrg_status xtrg_entanglement(xtrg_ctx* ctx, double* S, int n);
+
 /* Copy the current normalised rho to host memory.  bond_dims gets L+1 ints;
  * W[i] must hold bond_dims[i]*4*bond_dims[i+1] doubles (query the dims first
  * with W == NULL).  *lnc gets ln c, rho(beta) = e^{lnc} * rho. */
@@ -142,6 +152,21 @@ xtrg_status xtrg_get_state(xtrg_ctx* ctx, int* bond_dims, double* const* W, doub
 xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* rho, double lnc, double beta,
                            int right_canonical);
 
+/* Device-side checkpoint of the current state (rho, ln c, beta, doubling
+ * count): xtrg_checkpoint_save copies it into dev_buf, device memory of at
+ * least xtrg_checkpoint_bytes(ctx) bytes, 256-byte aligned, owned by the
+ * caller; xtrg_checkpoint_load makes a saved state the current one (same
+ * chain length, bonds within this context's capacity D* + 1), stream-ordered
+ * after the copies, so the next doubling continues from it.  A checkpoint is
+ * plain bytes: it may be copied to host memory or to another context of the
+ * same length and capacity.  Resuming from a checkpoint is exact (the saved
+ * tensors are the FP64 state).  Both calls synchronise the stream (save: its
+ * header is staged in host memory; load: the bond dimensions are read back).
+ * XTRG_ENOMEM: buffer too small; XTRG_EINVAL: not a checkpoint of this chain. */
+size_t xtrg_checkpoint_bytes(const xtrg_ctx* ctx);
+xtrg_status xtrg_checkpoint_save(xtrg_ctx* ctx, void* dev_buf, size_t bytes);
+xtrg_status xtrg_checkpoint_load(xtrg_ctx* ctx, const void* dev_buf, size_t bytes);
+
 typedef struct {
   double contraction_flops;  /* algorithmic 2*M*N*K of every contraction GEMM       */
   double split_flops;        /* estimated flops of the truncation (split)           */
@@ -153,14 +178,21 @@ typedef struct {
   long long exact_split_fallbacks; /* tensor-core-path updates that took the exact FP64 split */
   double split_ms;           /* device time of the tensor-core truncations (only while profiling) */
   long long orth_cluster_calls; /* orthonormalisations run as one thread-block cluster, all contexts */
+  double fp64_update_ms;     /* device time of the FP64-path two-site updates (only while profiling) */
+  long long fp64_updates_timed; /* FP64-path two-site updates timed (only while profiling) */
+  double fp64_env_pass_ms;   /* device time of the FP64-path initial right environments (profiling) */
+  long long orth_fallbacks;  /* tensor-core truncations whose CholeskyQR2 broke down and were
+                                orthonormalised by block Gram-Schmidt instead (this context) */
 } xtrg_stats;
 
-/* Counters since creation (kernel_launches: since the library was loaded). */
+/* Counters since creation (kernel_launches: since the library was loaded).
+ * Synchronises the context's stream (orth_fallbacks is counted on the device). */
 xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* out);
 
-/* on != 0: time every tensor-core GEMM launch with CUDA events on the
- * context's stream (adds event records; results resolved at the end of each
- * product, which synchronises anyway). */
+/* on != 0: time every tensor-core GEMM launch, every tensor-core truncation,
+ * every FP64-path two-site update and the FP64-path initial environment pass
+ * with CUDA events on the context's stream (adds event records; results are
+ * resolved at the end of each product, which then synchronises). */
 xtrg_status xtrg_set_profiling(xtrg_ctx* ctx, int on);
 
 /* The tensor-core contraction primitive behind the XTRG_BF16X* modes, exposed
@@ -176,6 +208,16 @@ size_t xtrg_tc_gemm_workspace_bytes(int M, int N, int K, int batch, int planes, 
 xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int N, int K,
                          int batch, int planes, int nprod, int splitk, void* workspace,
                          size_t workspace_bytes, void* cuda_stream);
+
+/* The same primitive for C[b] = A[b] * B[b] with B given row-major as
+ * batch x K x N (FP64, device): B's planes keep that layout and are staged
+ * into the tensor cores as an MN-major operand (no transpose pass).  Same
+ * precision, splitk and stream behaviour as xtrg_tc_gemm; workspace of at
+ * least xtrg_tc_gemm_nn_workspace_bytes() bytes, 256-byte aligned. */
+size_t xtrg_tc_gemm_nn_workspace_bytes(int M, int N, int K, int batch, int planes, int splitk);
+xtrg_status xtrg_tc_gemm_nn(const double* A, const double* B, double* C, int M, int N, int K,
+                            int batch, int planes, int nprod, int splitk, void* workspace,
+                            size_t workspace_bytes, void* cuda_stream);
 
 /* xtrg_tc_gemm for callers that cannot allocate device memory.  The paper has
  * no counterpart: this is a service of this library.  Same arguments,

@@ -25,7 +25,9 @@ SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "x
            "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_get_stats",
            "xtrg_set_profiling",
            "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm",
-           "xtrg_tc_gemm_static", "xtrg_batch_plan", "xtrg_batch_run"]
+           "xtrg_tc_gemm_static", "xtrg_batch_plan", "xtrg_batch_run", "xtrg_checkpoint_bytes",
+           "xtrg_checkpoint_save", "xtrg_checkpoint_load", "xtrg_entanglement",
+           "xtrg_tc_gemm_nn_workspace_bytes", "xtrg_tc_gemm_nn"]
 
 
 class xtrg_mpo(C.Structure):
@@ -55,7 +57,9 @@ class xtrg_stats(C.Structure):
                 ("tc_flops", C.c_double), ("tc_ms", C.c_double),
                 ("two_site_updates", C.c_longlong), ("tc_launches", C.c_longlong),
                 ("kernel_launches", C.c_longlong), ("exact_split_fallbacks", C.c_longlong),
-                ("split_ms", C.c_double), ("orth_cluster_calls", C.c_longlong)]
+                ("split_ms", C.c_double), ("orth_cluster_calls", C.c_longlong),
+                ("fp64_update_ms", C.c_double), ("fp64_updates_timed", C.c_longlong),
+                ("fp64_env_pass_ms", C.c_double), ("orth_fallbacks", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -110,6 +114,18 @@ def _load():
     lib.xtrg_tc_gemm_workspace_bytes.argtypes = [C.c_int] * 6
     lib.xtrg_tc_gemm.restype = C.c_int
     lib.xtrg_tc_gemm.argtypes = [P, P, P] + [C.c_int] * 7 + [P, C.c_size_t, P]
+    lib.xtrg_entanglement.restype = C.c_int
+    lib.xtrg_entanglement.argtypes = [P, C.POINTER(C.c_double), C.c_int]
+    lib.xtrg_checkpoint_bytes.restype = C.c_size_t
+    lib.xtrg_checkpoint_bytes.argtypes = [P]
+    lib.xtrg_checkpoint_save.restype = C.c_int
+    lib.xtrg_checkpoint_save.argtypes = [P, P, C.c_size_t]
+    lib.xtrg_checkpoint_load.restype = C.c_int
+    lib.xtrg_checkpoint_load.argtypes = [P, P, C.c_size_t]
+    lib.xtrg_tc_gemm_nn_workspace_bytes.restype = C.c_size_t
+    lib.xtrg_tc_gemm_nn_workspace_bytes.argtypes = [C.c_int] * 6
+    lib.xtrg_tc_gemm_nn.restype = C.c_int
+    lib.xtrg_tc_gemm_nn.argtypes = [P, P, P] + [C.c_int] * 7 + [P, C.c_size_t, P]
     lib.xtrg_tc_gemm_static.restype = C.c_int
     lib.xtrg_tc_gemm_static.argtypes = [P, P, P] + [C.c_int] * 7 + [P]
     return lib
@@ -196,6 +212,25 @@ def xtrg_set_state(ctx, sites, lnc, beta, right_canonical=False):
                                    1 if right_canonical else 0))
 
 
+def xtrg_entanglement(ctx, L):
+    """MPO entanglement S_E at bonds 1..L-1 (list of L-1 floats)."""
+    out = (C.c_double * max(1, L - 1))()
+    _check(ctx, LIB.xtrg_entanglement(ctx, out, L - 1))
+    return [out[i] for i in range(L - 1)]
+
+
+def xtrg_checkpoint_bytes(ctx) -> int:
+    return int(LIB.xtrg_checkpoint_bytes(ctx))
+
+
+def xtrg_checkpoint_save(ctx, dev_ptr, nbytes):
+    _check(ctx, LIB.xtrg_checkpoint_save(ctx, C.c_void_p(dev_ptr), C.c_size_t(nbytes)))
+
+
+def xtrg_checkpoint_load(ctx, dev_ptr, nbytes):
+    _check(ctx, LIB.xtrg_checkpoint_load(ctx, C.c_void_p(dev_ptr), C.c_size_t(nbytes)))
+
+
 def xtrg_get_stats(ctx) -> dict:
     o = xtrg_stats()
     _check(ctx, LIB.xtrg_get_stats(ctx, C.byref(o)))
@@ -218,6 +253,20 @@ def xtrg_tc_gemm(A_ptr, B_ptr, C_ptr, M, N, K, batch, planes, nprod, splitk, ws_
                          C.c_void_p(stream))
     if s != XTRG_OK:
         raise XtrgError(s, "xtrg_tc_gemm")
+
+
+def xtrg_tc_gemm_nn_workspace_bytes(M, N, K, batch, planes, splitk) -> int:
+    return int(LIB.xtrg_tc_gemm_nn_workspace_bytes(M, N, K, batch, planes, splitk))
+
+
+def xtrg_tc_gemm_nn(A_ptr, B_ptr, C_ptr, M, N, K, batch, planes, nprod, splitk, ws_ptr, ws_bytes,
+                    stream):
+    """Device pointers in, status checked; C = A * B per batch, B given K x N."""
+    s = LIB.xtrg_tc_gemm_nn(C.c_void_p(A_ptr), C.c_void_p(B_ptr), C.c_void_p(C_ptr), M, N, K,
+                            batch, planes, nprod, splitk, C.c_void_p(ws_ptr), C.c_size_t(ws_bytes),
+                            C.c_void_p(stream))
+    if s != XTRG_OK:
+        raise XtrgError(s, "xtrg_tc_gemm_nn")
 
 
 def xtrg_tc_gemm_static(A_ptr, B_ptr, C_ptr, M, N, K, batch, planes, nprod, splitk, stream):

@@ -1,6 +1,7 @@
 // Layout and precision conversions of the tensor-core path: FP64 tensors to
-// BF16 split planes through strided views, plane-preserving re-layouts, and
-// the FP64 reduction of split-K partial sums.
+// BF16 split planes through strided views, and the FP64 reduction of split-K
+// partial sums (alone, or fused with the planes of the result in both
+// orientations).
 #include <cuda_bf16.h>
 
 #include "mixed_ops.cuh"
@@ -39,41 +40,6 @@ __global__ void to_planes_kernel(const S* __restrict__ src, Idx3 rv, Idx3 kv, lo
   }
 }
 
-__global__ void relayout_planes_kernel(const __nv_bfloat16* __restrict__ src, Idx3 rv, Idx3 kv,
-                                       int rows, int K, __nv_bfloat16* __restrict__ out,
-                                       long long ld, int planes, long long sps, long long ops) {
-  const long long per = (long long)rows * ld;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / ld), k = (int)(e % ld);
-    const long long so = (k < K) ? idx_off(rv, r) + idx_off(kv, k) : -1;
-    for (int p = 0; p < planes; ++p)
-      out[e + p * ops] = so >= 0 ? src[so + p * sps] : __float2bfloat16_rn(0.f);
-  }
-}
-
-// out[p][r][k] = src[p][k][r] for r < rows, k < K (32 x 32 tiles through shared
-// memory, coalesced on both sides); padding columns K <= k < ld are zeroed.
-__global__ void transpose_planes_kernel(const __nv_bfloat16* __restrict__ src, long long sld,
-                                        int rows, int K, __nv_bfloat16* __restrict__ out,
-                                        long long ld, long long sps, long long ops) {
-  __shared__ __nv_bfloat16 tile[32][33];
-  const int p = blockIdx.z;
-  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  const __nv_bfloat16* sp = src + p * sps;
-  __nv_bfloat16* op = out + p * ops;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8 threads
-  for (int y = ty; y < 32; y += 8) {
-    const int k = k0 + y, r = r0 + tx;
-    tile[y][tx] = (k < K && r < rows) ? sp[(long long)k * sld + r] : __float2bfloat16_rn(0.f);
-  }
-  __syncthreads();
-  for (int y = ty; y < 32; y += 8) {
-    const int r = r0 + y, k = k0 + tx;
-    if (r < rows && k < ld) op[(long long)r * ld + k] = tile[tx][y];
-  }
-}
-
 __global__ void reduce_partials_kernel(const float* __restrict__ part, int splits, long long n,
                                        double* __restrict__ out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -84,11 +50,71 @@ __global__ void reduce_partials_kernel(const float* __restrict__ part, int split
   }
 }
 
-__global__ void f32_to_f64_kernel(const float* __restrict__ a, long long n, double* __restrict__ b) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x)
-    b[e] = (double)a[e];
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& p0, __nv_bfloat16& p1,
+                                       __nv_bfloat16& p2) {
+  p0 = __double2bfloat16(x);
+  const double r1 = x - (double)__bfloat162float(p0);
+  p1 = __double2bfloat16(r1);
+  p2 = __double2bfloat16(r1 - (double)__bfloat162float(p1));
 }
+
+// One 32 x 32 tile of C = sum of the split-K partials: the FP64 result, its
+// three BF16 planes in both orientations (row-major [m][ldn] and transposed
+// [n][ldm], the K-major operands of C x and C^T x), and the tile's sum of
+// squares added into *ss.  The transposed planes go through shared memory so
+// that both the reads and the writes are coalesced; padding columns of both
+// plane layouts are written as zero.
+__global__ void reduce_partials_planes_kernel(const float* __restrict__ part, int splits, int m,
+                                              int n, double* __restrict__ out,
+                                              __nv_bfloat16* __restrict__ prm, long long ldn,
+                                              __nv_bfloat16* __restrict__ ptr, long long ldm,
+                                              long long ps, double* ss) {
+  __shared__ double tile[32][33];
+  __shared__ double red[8];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8 threads
+  const int n0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  const long long mn = (long long)m * n;
+  double acc = 0.0;
+  for (int y = ty; y < 32; y += 8) {
+    const int r = m0 + y, c = n0 + tx;
+    double v = 0.0;
+    if (r < m && c < n) {
+      const long long e = (long long)r * n + c;
+      for (int i = 0; i < splits; ++i) v += (double)part[i * mn + e];
+      out[e] = v;
+      acc = fma(v, v, acc);
+    }
+    tile[y][tx] = v;
+    if (r < m && c < ldn) {
+      __nv_bfloat16 a, b, d;
+      split3(v, a, b, d);
+      const long long o = (long long)r * ldn + c;
+      prm[o] = a;
+      prm[o + ps] = b;
+      prm[o + 2 * ps] = d;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (tx == 0) red[ty] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    atomicAdd(ss, t);
+  }
+  for (int y = ty; y < 32; y += 8) {
+    const int r = n0 + y, c = m0 + tx;   // row r of C^T, column c
+    if (r < n && c < ldm) {
+      __nv_bfloat16 a, b, d;
+      split3(c < m ? tile[tx][y] : 0.0, a, b, d);
+      const long long o = (long long)r * ldm + c;
+      ptr[o] = a;
+      ptr[o + ps] = b;
+      ptr[o + 2 * ps] = d;
+    }
+  }
+}
+
 
 }  // namespace
 
@@ -114,27 +140,6 @@ cudaError_t to_planes_f32(const float* src, Idx3 rv, Idx3 kv, long long sbs, int
   return cudaGetLastError();
 }
 
-cudaError_t transpose_planes(const __nv_bfloat16* src, long long sld, int rows, int K,
-                             __nv_bfloat16* out, long long ld, int planes, long long sps,
-                             long long ops, cudaStream_t st) {
-  if (rows <= 0 || ld <= 0) return cudaSuccess;
-  dim3 grid((rows + 31) / 32, (int)((ld + 31) / 32), planes);
-  note_launch();
-  transpose_planes_kernel<<<grid, 256, 0, st>>>(src, sld, rows, K, out, ld, sps, ops);
-  return cudaGetLastError();
-}
-
-cudaError_t relayout_planes(const __nv_bfloat16* src, Idx3 rv, Idx3 kv, int rows, int K,
-                            __nv_bfloat16* out, long long ld, int planes, long long sps,
-                            long long ops, cudaStream_t st) {
-  long long total = (long long)rows * ld;
-  if (total <= 0) return cudaSuccess;
-  note_launch();
-  relayout_planes_kernel<<<grid_for(total), 256, 0, st>>>(src, rv, kv, rows, K, out, ld, planes,
-                                                          sps, ops);
-  return cudaGetLastError();
-}
-
 cudaError_t reduce_partials(const float* part, int splits, long long n, double* out,
                             cudaStream_t st) {
   note_launch();
@@ -142,8 +147,16 @@ cudaError_t reduce_partials(const float* part, int splits, long long n, double* 
   return cudaGetLastError();
 }
 
-cudaError_t f32_to_f64(const float* a, long long n, double* b, cudaStream_t st) {
+
+cudaError_t reduce_partials_planes(const float* part, int splits, int m, int n, double* out,
+                                   __nv_bfloat16* prm, long long ldn, __nv_bfloat16* ptr,
+                                   long long ldm, long long ps, double* ss, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(ss, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
   note_launch();
-  f32_to_f64_kernel<<<grid_for(n), 256, 0, st>>>(a, n, b);
+  reduce_partials_planes_kernel<<<grid, 256, 0, st>>>(part, splits, m, n, out, prm, ldn, ptr, ldm,
+                                                      ps, ss);
   return cudaGetLastError();
 }

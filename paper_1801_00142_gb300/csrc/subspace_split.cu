@@ -12,7 +12,12 @@
 // term eta R keeps every column of Y away from exact zero; directions it adds
 // carry weight below eta^2 relative.
 //
-// orth() is block classical Gram-Schmidt over panels of 32 columns: two FP32
+// orth() is first tried as a scaled CholeskyQR2 of the whole block (tensor-core
+// Gram, one-CTA FP32 Cholesky, all-SM triangular solve; see below), which is
+// exact in the subspace and fast when the columns, scaled to unit norm, are
+// well conditioned, as they are once the warm start has converged.  When a
+// pivot shows that they are not, the fallback is block classical
+// Gram-Schmidt over panels of 32 columns: two FP32
 // projection passes against the earlier panels, then CholeskyQR2 inside the
 // panel with the 32 x 32 Gram and its Cholesky factor in FP64 (or, in the
 // cluster kernel below, a double-float Gram and FP64 Cholesky).  Columns whose
@@ -67,8 +72,10 @@ __global__ void warm_start_kernel(const double* __restrict__ S, long long sj, lo
   }
 }
 
-__global__ void add_noise_kernel(float* __restrict__ Y, long long n, float eta,
-                                 unsigned long long seed) {
+// Y += eta R with eta = 1e-5 * rms(C_E), rms from ||C_E||^2 on the device
+__global__ void add_noise_kernel(float* __restrict__ Y, long long n, const double* __restrict__ tot,
+                                 double inv_mn, unsigned long long seed) {
+  const float eta = (float)(1e-5 * sqrt(*tot * inv_mn));
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
     Y[e] += eta * hash_uniform(seed ^ (0xD1B54A32D192ED03ull * (e + 1)));
@@ -123,6 +130,7 @@ struct OrthArgs {
   double* redd;      // [PANEL * PANEL] reduced Gram (FP64)
   unsigned* bar;     // [0] arrivals, [1] generation
   int* status;       // 0 ok, 1 barrier timeout
+  const int* run_if; // null, or run only if *run_if != 0 (the fast path broke down)
 };
 
 // grid barrier with a bounded wait (false: timed out, every CTA leaves)
@@ -204,6 +212,11 @@ __device__ void reduce_partials_grid_f64(const OrthArgs& a, int n, float* scratc
 }
 
 __global__ void __launch_bounds__(ORTH_NT) orth_persistent(OrthArgs a) {
+  if (a.run_if) {
+    if (*a.run_if == 0) return;   // every CTA leaves before any barrier
+    // run_if[1] counts the orthonormalisations the fast path handed over
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(const_cast<int*>(a.run_if) + 1, 1);
+  }
   __shared__ float Ys[ROWS_PER_CTA][MAX_K + 1];
   __shared__ __align__(16) float Ss[MAX_K * PANEL];
   __shared__ double Ld[PANEL][PANEL + 1];
@@ -332,6 +345,7 @@ constexpr int OC_OUT = OC_RMAX * PANEL / OC_NT;  // panel outputs per thread
 struct OrthClusterArgs {
   float* Y;
   int rows, k, rpc;   // rpc: rows per CTA (<= OC_RMAX)
+  const int* run_if;  // null, or run only if *run_if != 0 (the fast path broke down)
 };
 
 // s + e = a + b exactly (round-to-nearest adds, never contracted)
@@ -360,6 +374,12 @@ size_t orth_cluster_smem(int k) {
 }
 
 __global__ void __launch_bounds__(OC_NT, 1) orth_cluster(OrthClusterArgs a) {
+  // every CTA of the cluster reads the same flag and leaves before any barrier
+  if (a.run_if) {
+    if (*a.run_if == 0) return;
+    // run_if[1] counts the orthonormalisations the fast path handed over
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(const_cast<int*>(a.run_if) + 1, 1);
+  }
   extern __shared__ __align__(16) unsigned char oc_smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x;
@@ -596,14 +616,270 @@ OrthSetup orth_setup() {
     if (_e != cudaSuccess) return _e;          \
   } while (0)
 
+// C (M x N, FP32 row-major, ldc) = A B^T on the tensor cores (3 planes, 6
+// products).  Each operand is either given as BF16 planes already (p: row
+// stride pld, plane stride pps) or as an FP32 view split by to_planes_f32.
+struct View {
+  const float* f;
+  Idx3 rv, kv;
+  const __nv_bfloat16* p;
+  long long pld, pps;
+};
+
+View planes_view(const __nv_bfloat16* p, long long pld, long long pps) {
+  return View{nullptr, idx_plain(0), idx_plain(0), p, pld, pps};
+}
+View f32_view(const float* f, Idx3 rv, Idx3 kv) { return View{f, rv, kv, nullptr, 0, 0}; }
+
+cudaError_t tc_product(const View& a, const View& b, int M, int N, int K, float* C, long long ldc,
+                       const SubspaceBuffers& buf, cudaStream_t st) {
+  const long long ld = tc_ld(K);
+  const long long psa = (long long)M * ld, psb = (long long)N * ld;
+  if (psa > buf.psa || psb > buf.psb) return cudaErrorInvalidValue;
+  TcOperand A{buf.pa, 3, M, K, ld, 0, buf.psa, 1};
+  TcOperand B{buf.pb, 3, N, K, ld, 0, buf.psb, 1};
+  if (a.p) A = TcOperand{a.p, 3, M, K, a.pld, 0, a.pps, 1};
+  else RET(to_planes_f32(a.f, a.rv, a.kv, 0, M, K, 1, buf.pa, ld, 0, 3, buf.psa, st));
+  if (b.p) B = TcOperand{b.p, 3, N, K, b.pld, 0, b.pps, 1};
+  else RET(to_planes_f32(b.f, b.rv, b.kv, 0, N, K, 1, buf.pb, ld, 0, 3, buf.psb, st));
+  TcOutput o;
+  memset(&o, 0, sizeof o);
+  o.mode = TC_OUT_F32;
+  o.f32 = C;
+  o.cm = idx_plain(ldc);
+  o.cn = idx_plain(1);
+  o.alpha = 1.0;
+  return tc_gemm(A, B, M, N, K, 1, 6, 1, o, buf.err, st);
+}
+
+// ---------------------------------------------------------------------------
+// Fast path of the orthonormalisation: scaled CholeskyQR2.
+//
+// Y = C_E V_prev + eta R has columns of very different norms (they follow
+// the singular values of C_E), but once the warm start has converged they
+// are close to orthogonal.  With the column scaling D = diag(1/||y_j||) the
+// Gram G = D Y^T Y D is then well conditioned, and two CholeskyQR passes
+// (G = L L^T, U = Y D L^{-T}) give an orthonormal U to FP32 level.  The
+// Gram runs on the tensor cores (tc_product, 24-bit products, unbiased
+// FP32 accumulation), the k x k Cholesky on one CTA in FP32 (blocked
+// right-looking, packed lower triangle in shared memory), and the
+// triangular solve on every SM (one warp per row, blocks of 32 columns).
+// A scaled pivot below tau means Y is ill conditioned (a warm start far
+// from converged, a growing bond): the factor kernel raises *flag and the
+// block Gram-Schmidt kernels, launched after it, orthonormalise the
+// untouched Y instead (they return at once when *flag is 0).  A column
+// whose norm is zero is dead: its output column is zero, as in the block
+// Gram-Schmidt kernels.
+constexpr int CQ_NT = 1024;       // threads of the factor kernel
+constexpr int CQ_SOLVE_NT = 256;  // threads of the solve kernel (8 warps, one row each)
+constexpr int CQ_PLD = 33;        // row stride of the panel copy
+
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+size_t cholqr_factor_smem(int k) {
+  const size_t packed = ((size_t)k * (k + 1) / 2 + 3) / 4 * 4;
+  return (packed + (size_t)MAX_K * CQ_PLD + 2 * MAX_K) * 4;
+}
+
+// G (k x k FP32 row-major, symmetric; lower triangle read) -> Lout (packed
+// lower Cholesky factor of D G D), dout (the scaling d_j; 0 for a dead
+// column), linv (1 / L_jj, 0 for a dead column); *flag = 1 if a live
+// scaled pivot falls below tau (never cleared here).
+__global__ void __launch_bounds__(CQ_NT, 1)
+    cholqr_factor(const float* __restrict__ G, int k, float tau, float* __restrict__ Lout,
+                  float* __restrict__ dout, float* __restrict__ linv_out, int* flag) {
+  extern __shared__ __align__(16) float cq[];
+  const int np = k * (k + 1) / 2;
+  float* A = cq;                                    // packed lower triangle
+  float* P = cq + ((np + 3) / 4 * 4);               // panel copy [MAX_K][CQ_PLD]
+  float* d = P + MAX_K * CQ_PLD;                    // scaling
+  float* li = d + MAX_K;                            // 1 / L_jj
+  __shared__ float red[32];
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  // largest diagonal entry, for the dead-column threshold
+  float gm = 0.f;
+  for (int j = tid; j < k; j += CQ_NT) {
+    const float g = G[(long long)j * k + j];
+    gm = fmaxf(gm, (g == g) ? g : 3.0e38f);
+  }
+  for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  if (lane == 0) red[warp] = gm;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  if (tid < 32) {
+    float v = red[tid];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (tid == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float gmax = red[0];
+  for (int j = tid; j < k; j += CQ_NT) {
+    const float g = G[(long long)j * k + j];
+    d[j] = (g > 1e-30f * gmax && g < 3.0e38f) ? 1.f / sqrtf(g) : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < np; e += CQ_NT) {
+    // e -> (i, j), j <= i
+    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while (i * (i + 1) / 2 > e) --i;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    const int j = e - i * (i + 1) / 2;
+    const float v = G[(long long)i * k + j] * d[i] * d[j];
+    A[e] = (v == v) ? v : 0.f;
+    if (v != v) bad = 1;
+  }
+  __syncthreads();
+  for (int p0 = 0; p0 < k; p0 += 32) {
+    const int pw = min(32, k - p0);
+    // (a) the diagonal block, warp 0 (lane = row inside the block)
+    if (warp == 0) {
+      for (int j = 0; j < pw; ++j) {
+        const int jj = p0 + j;
+        const float piv = A[pk(jj, jj)];
+        __syncwarp();   // every lane has read the pivot before lane 0 overwrites it
+        const bool dead = d[jj] == 0.f;
+        const bool broke = !dead && !(piv > tau);
+        const float ljj = (dead || broke) ? 1.f : sqrtf(piv);
+        const float inv = (dead || broke) ? 0.f : 1.f / ljj;
+        if (lane == 0) {
+          A[pk(jj, jj)] = ljj;
+          li[jj] = inv;
+          if (broke) bad = 1;
+        }
+        __syncwarp();
+        const int i = p0 + lane;
+        if (lane > j && lane < pw) A[pk(i, jj)] *= inv;
+        __syncwarp();
+        if (lane > j && lane < pw) {
+          const float lij = A[pk(i, jj)];
+          for (int c = j + 1; c <= lane; ++c) A[pk(i, p0 + c)] -= lij * A[pk(p0 + c, jj)];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // (b) the rows below the block: L_ip = A_ip L_pp^{-T}, copied to the panel buffer
+    for (int i = p0 + pw + tid; i < k; i += CQ_NT) {
+      float x[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        if (t < pw) {
+          float v = A[pk(i, p0 + t)];
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (q < t) v -= x[q] * A[pk(p0 + t, p0 + q)];
+          x[t] = v * li[p0 + t];
+          A[pk(i, p0 + t)] = x[t];
+          P[i * CQ_PLD + t] = x[t];
+        }
+      }
+    }
+    __syncthreads();
+    // (c) trailing update A_ic -= sum_t L_it L_ct for p0+pw <= c <= i, in
+    // 4 x 4 register blocks of the lower triangle
+    const int r0 = p0 + pw, n = k - r0;
+    if (n > 0) {
+      const int nb = (n + 3) / 4, nblk = nb * (nb + 1) / 2;
+      for (int bidx = tid; bidx < nblk; bidx += CQ_NT) {
+        int bi = (int)((sqrtf(8.f * (float)bidx + 1.f) - 1.f) * 0.5f);
+        while (bi * (bi + 1) / 2 > bidx) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= bidx) ++bi;
+        const int bc = bidx - bi * (bi + 1) / 2;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        const int i0 = r0 + 4 * bi, c0 = r0 + 4 * bc;
+        for (int t = 0; t < pw; ++t) {
+          float pi[4], pc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            pi[u] = (i0 + u < k) ? P[(i0 + u) * CQ_PLD + t] : 0.f;
+            pc[u] = (c0 + u < k) ? P[(c0 + u) * CQ_PLD + t] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pi[u], pc[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int i = i0 + u, c = c0 + v;
+            if (i < k && c <= i) A[pk(i, c)] -= acc[u][v];
+          }
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < np; e += CQ_NT) Lout[e] = A[e];
+  for (int j = tid; j < k; j += CQ_NT) {
+    dout[j] = d[j];
+    linv_out[j] = li[j];
+  }
+  if (tid == 0 && bad) atomicExch(flag, 1);
+}
+
+// U[r] = (Y[r] o d) L^{-T} for every row r (one warp per row): with u L^T = z,
+// u_j = (z_j - sum_{i<j} u_i L_ji) / L_jj, in blocks of 32 columns (earlier
+// blocks first, then a sequential solve inside the block).  Does nothing if
+// *flag is set (the fast path broke down).
+__global__ void __launch_bounds__(CQ_SOLVE_NT)
+    cholqr_solve(const float* __restrict__ Y, int rows, int k, const float* __restrict__ Lp,
+                 const float* __restrict__ dv, const float* __restrict__ linv,
+                 const int* __restrict__ flag, float* __restrict__ U) {
+  if (*flag) return;
+  extern __shared__ __align__(16) float Ls[];
+  const int np = k * (k + 1) / 2;
+  for (int e = threadIdx.x; e < np; e += CQ_SOLVE_NT) Ls[e] = Lp[e];
+  __syncthreads();
+  const int lane = threadIdx.x % 32;
+  const int WPB = CQ_SOLVE_NT / 32;
+  for (int r = blockIdx.x * WPB + threadIdx.x / 32; r < rows; r += gridDim.x * WPB) {
+    float x[MAX_K / 32];
+#pragma unroll
+    for (int qb = 0; qb < MAX_K / 32; ++qb) {
+      x[qb] = 0.f;
+      if (qb * 32 < k) {
+        const int j = qb * 32 + lane;
+        float s = (j < k) ? Y[(long long)r * k + j] * dv[j] : 0.f;
+        // earlier blocks
+#pragma unroll
+        for (int q = 0; q < MAX_K / 32; ++q) {
+          if (q < qb) {
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) {
+              const float xt = __shfl_sync(0xffffffffu, x[q], t);
+              if (j < k) s = fmaf(-xt, Ls[pk(j, q * 32 + t)], s);
+            }
+          }
+        }
+        // inside the block
+        float xj = 0.f;
+        for (int t = 0; t < 32 && qb * 32 + t < k; ++t) {
+          if (lane == t) xj = s * linv[j];
+          const float xt = __shfl_sync(0xffffffffu, xj, t);
+          if (lane > t && j < k) s = fmaf(-xt, Ls[pk(j, qb * 32 + t)], s);
+        }
+        x[qb] = xj;
+        if (j < k) U[(long long)r * k + j] = xj;
+      }
+    }
+  }
+}
+
 // Y (rows x k, row-major FP32) <- orthonormal basis of its column space.
 cudaError_t orth_check(const float* Q, int rows, int k, const SubspaceBuffers& b, cudaStream_t st);
 
-cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
+cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st,
+                      const int* run_if) {
   if (k > MAX_K) return cudaErrorInvalidValue;
   if (rows <= OC_NC * OC_RMAX && orth_cluster_available()) {
     OrthClusterArgs ca;
-    ca.Y = Y; ca.rows = rows; ca.k = k;
+    ca.Y = Y; ca.rows = rows; ca.k = k; ca.run_if = run_if;
     ca.rpc = (rows + OC_NC - 1) / OC_NC;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = orth_cluster_config(orth_cluster_smem(k), st, attr);
@@ -625,11 +901,62 @@ cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaS
   a.part = b.orth_part; a.red = b.orth_red;
   a.partd = b.orth_partd; a.redd = b.orth_redd;
   a.bar = b.orth_bar; a.status = (int*)(b.orth_bar + 2);
+  a.run_if = run_if;
   RET(cudaMemsetAsync(b.orth_bar, 0, 4 * sizeof(unsigned), st));
   void* args[] = {&a};
   note_launch();
   RET(cudaLaunchCooperativeKernel((void*)orth_persistent, dim3(G), dim3(ORTH_NT), args, 0, st));
   return cudaSuccess;
+}
+
+// shared-memory opt-in of the two CholeskyQR kernels, once per device
+PerDevice<cudaError_t> g_cholqr_setup;
+
+cudaError_t cholqr_setup() {
+  cudaError_t r = cudaSuccess;
+  cudaError_t e = g_cholqr_setup.get(
+      [](int) {
+        cudaError_t x = cudaFuncSetAttribute(cholqr_factor,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)cholqr_factor_smem(MAX_K));
+        if (x == cudaSuccess)
+          x = cudaFuncSetAttribute(cholqr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((size_t)MAX_K * (MAX_K + 1) / 2 * 4));
+        return x;
+      },
+      &r);
+  return e != cudaSuccess ? e : r;
+}
+
+// Y (rows x k, FP32) <- an orthonormal basis of its columns: scaled
+// CholeskyQR2 (Y -> U1 in b.Q -> Y), with the block Gram-Schmidt kernels as
+// the device-side fallback when a pass breaks down (see cholqr_factor).
+cudaError_t orthonormalise(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
+  if (k > MAX_K) return cudaErrorInvalidValue;
+  RET(cholqr_setup());
+  RET(cudaMemsetAsync(b.chol_flag, 0, sizeof(int), st));
+  const size_t fsm = cholqr_factor_smem(k), ssm = (size_t)k * (k + 1) / 2 * 4;
+  const int wpb = CQ_SOLVE_NT / 32;
+  int grid = (rows + wpb - 1) / wpb;
+  if (grid > 152) grid = 152;
+  const float* src = Y;
+  float* dst = b.Q;
+  for (int pass = 0; pass < 2; ++pass) {
+    // G = Y^T Y (k x k) on the tensor cores
+    RET(tc_product(f32_view(src, idx_plain(1), idx_plain(k)), f32_view(src, idx_plain(1), idx_plain(k)),
+                   k, k, rows, b.out, k, b, st));
+    note_launch();
+    cholqr_factor<<<1, CQ_NT, fsm, st>>>(b.out, k, pass == 0 ? 1e-6f : 0.25f, b.chol_L, b.chol_d,
+                                         b.chol_li, b.chol_flag);
+    RET(cudaGetLastError());
+    note_launch();
+    cholqr_solve<<<grid, CQ_SOLVE_NT, ssm, st>>>(src, rows, k, b.chol_L, b.chol_d, b.chol_li,
+                                                 b.chol_flag, dst);
+    RET(cudaGetLastError());
+    src = b.Q;
+    dst = Y;
+  }
+  return block_cgs(Y, rows, k, b, st, b.chol_flag);
 }
 
 }  // namespace
@@ -640,35 +967,6 @@ size_t subspace_plane_elems_a(int cap) { return 3 * (size_t)(4 * cap) * tc_ld(4 
 size_t subspace_plane_elems_b(int cap) { return 3 * (size_t)(4 * cap) * tc_ld(4 * cap); }
 
 namespace {
-// C (M x N, FP32 row-major, ldc) = A B^T on the tensor cores, A and B given as
-// FP64 or FP32 views through to_planes (3 planes, 6 products).
-struct View {
-  const double* d;
-  const float* f;
-  Idx3 rv, kv;
-};
-
-cudaError_t tc_product(const View& a, const View& b, int M, int N, int K, float* C, long long ldc,
-                       const SubspaceBuffers& buf, cudaStream_t st) {
-  const long long ld = tc_ld(K);
-  const long long psa = (long long)M * ld, psb = (long long)N * ld;
-  if (psa > buf.psa || psb > buf.psb) return cudaErrorInvalidValue;
-  if (a.d) RET(to_planes(a.d, a.rv, a.kv, 0, M, K, 1, buf.pa, ld, 0, 3, buf.psa, st));
-  else RET(to_planes_f32(a.f, a.rv, a.kv, 0, M, K, 1, buf.pa, ld, 0, 3, buf.psa, st));
-  if (b.d) RET(to_planes(b.d, b.rv, b.kv, 0, N, K, 1, buf.pb, ld, 0, 3, buf.psb, st));
-  else RET(to_planes_f32(b.f, b.rv, b.kv, 0, N, K, 1, buf.pb, ld, 0, 3, buf.psb, st));
-  TcOperand A{buf.pa, 3, M, K, ld, 0, buf.psa, 1};
-  TcOperand B{buf.pb, 3, N, K, ld, 0, buf.psb, 1};
-  TcOutput o;
-  memset(&o, 0, sizeof o);
-  o.mode = TC_OUT_F32;
-  o.f32 = C;
-  o.cm = idx_plain(ldc);
-  o.cn = idx_plain(1);
-  o.alpha = 1.0;
-  return tc_gemm(A, B, M, N, K, 1, 6, 1, o, buf.err, st);
-}
-
 // max over live columns of |Q^T Q - I| (dead columns, norm < 1/2, are skipped)
 // into b.dscal[2] (as FP64).  Q^T Q by the tensor cores, 6 products.
 __global__ void orth_defect_kernel(const float* __restrict__ G, int k, double* out) {
@@ -692,8 +990,8 @@ __global__ void orth_defect_kernel(const float* __restrict__ G, int k, double* o
 }
 
 cudaError_t orth_check(const float* Q, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
-  RET(tc_product(View{nullptr, Q, idx_plain(1), idx_plain(k)},
-                 View{nullptr, Q, idx_plain(1), idx_plain(k)}, k, k, rows, b.out, k, b, st));
+  RET(tc_product(f32_view(Q, idx_plain(1), idx_plain(k)), f32_view(Q, idx_plain(1), idx_plain(k)),
+                 k, k, rows, b.out, k, b, st));
   note_launch();
   orth_defect_kernel<<<1, 1024, 0, st>>>(b.out, k, b.dscal + 2);
   return cudaGetLastError();
@@ -715,37 +1013,31 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
                            const double* warm, int kold, double* left, double* right,
                            unsigned long long seed, const SubspaceBuffers& b, cudaStream_t st,
                            double* discarded, double* orth_defect) {
+  (void)CE;
   if (k > 256 || k > m || k > n) return cudaErrorInvalidValue;
-  const long long mn = (long long)m * n;
-  // ||C_E||^2 (FP64)
-  RET(cudaMemsetAsync(b.dscal, 0, 3 * sizeof(double), st));
-  note_launch();
-  sumsq_f64_kernel<<<grid_for(mn) < 304 ? grid_for(mn) : 304, 256, 0, st>>>(CE, mn, b.dscal);
-  RET(cudaGetLastError());
-  double tot = 0.0;
-  RET(cudaMemcpyAsync(&tot, b.dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
-  RET(cudaStreamSynchronize(st));
-  const float eta = (float)(1e-5 * sqrt(tot / ((double)m * n)));
+  const double inv_mn = 1.0 / ((double)m * n);
+  const long long ldn = tc_ld(n), ldm = tc_ld(m);
+  const View ce = planes_view(b.ce_rm, ldn, b.ce_ps);    // C_E   (m rows, K = n)
+  const View cet = planes_view(b.ce_tr, ldm, b.ce_ps);   // C_E^T (n rows, K = m)
+  RET(cudaMemsetAsync(b.dscal + 1, 0, 2 * sizeof(double), st));
   if (dir_right) {
     // warm start: rows of the current C_{i+1} (kold x n) -> Q (n x k)
     note_launch();
     warm_start_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(warm, n, 1, kold, n, k, seed,
                                                                   b.Q);
     // Y = C_E Q (m x k): A = C_E (m rows, K = n), B = Q^T (k rows, K = n)
-    RET(tc_product(View{CE, nullptr, idx_plain(n), idx_plain(1)},
-                   View{nullptr, b.Q, idx_plain(1), idx_plain(k)}, m, k, n, b.Y, k, b, st));
+    RET(tc_product(ce, f32_view(b.Q, idx_plain(1), idx_plain(k)), m, k, n, b.Y, k, b, st));
     note_launch();
-    add_noise_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.Y, (long long)m * k, eta,
-                                                                 seed + 7);
+    add_noise_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.Y, (long long)m * k, b.ce_ss,
+                                                                 inv_mn, seed + 7);
     RET(cudaGetLastError());
-    RET(block_cgs(b.Y, m, k, b, st));
+    RET(orthonormalise(b.Y, m, k, b, st));
     RET(orth_check(b.Y, m, k, b, st));
     // C_i = U (m x k); C_{i+1} = U^T C_E (k x n)
     note_launch();
     copy_f2d_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.Y, (long long)m * k, left);
     // U^T C_E (k x n): A = U^T (k rows, K = m), B = C_E^T (n rows, K = m)
-    RET(tc_product(View{nullptr, b.Y, idx_plain(1), idx_plain(k)},
-                   View{CE, nullptr, idx_plain(1), idx_plain(n)}, k, n, m, b.out, n, b, st));
+    RET(tc_product(f32_view(b.Y, idx_plain(1), idx_plain(k)), cet, k, n, m, b.out, n, b, st));
     note_launch();
     copy_f2d_kernel<<<grid_for((long long)k * n), 256, 0, st>>>(b.out, (long long)k * n, right);
     RET(cudaGetLastError());
@@ -755,35 +1047,35 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
     warm_start_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(warm, 1, kold, kold, m, k, seed,
                                                                   b.Q);
     // Z = C_E^T Q (n x k): A = C_E^T (n rows, K = m), B = Q^T (k rows, K = m)
-    RET(tc_product(View{CE, nullptr, idx_plain(1), idx_plain(n)},
-                   View{nullptr, b.Q, idx_plain(1), idx_plain(k)}, n, k, m, b.Y, k, b, st));
+    RET(tc_product(cet, f32_view(b.Q, idx_plain(1), idx_plain(k)), n, k, m, b.Y, k, b, st));
     note_launch();
-    add_noise_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(b.Y, (long long)n * k, eta,
-                                                                 seed + 7);
+    add_noise_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(b.Y, (long long)n * k, b.ce_ss,
+                                                                 inv_mn, seed + 7);
     RET(cudaGetLastError());
-    RET(block_cgs(b.Y, n, k, b, st));
+    RET(orthonormalise(b.Y, n, k, b, st));
     RET(orth_check(b.Y, n, k, b, st));
     // C_{i+1} = V^T (k x n); C_i = C_E V (m x k)
     note_launch();
     transpose_f2d_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(b.Y, n, k, right);
     // C_E V (m x k): A = C_E (m rows, K = n), B = V^T (k rows, K = n)
-    RET(tc_product(View{CE, nullptr, idx_plain(n), idx_plain(1)},
-                   View{nullptr, b.Y, idx_plain(1), idx_plain(k)}, m, k, n, b.out, k, b, st));
+    RET(tc_product(ce, f32_view(b.Y, idx_plain(1), idx_plain(k)), m, k, n, b.out, k, b, st));
     note_launch();
     copy_f2d_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.out, (long long)m * k, left);
     RET(cudaGetLastError());
   }
-  // discarded weight = 1 - ||centre||^2 / ||C_E||^2
+  // discarded weight = 1 - ||centre||^2 / ||C_E||^2; the one host read of the update
   double* centre = dir_right ? right : left;
   const long long nc = dir_right ? (long long)k * n : (long long)m * k;
   note_launch();
   sumsq_f64_kernel<<<grid_for(nc) < 304 ? grid_for(nc) : 304, 256, 0, st>>>(centre, nc,
                                                                             b.dscal + 1);
   RET(cudaGetLastError());
-  double h[2] = {0.0, 0.0};
-  RET(cudaMemcpyAsync(h, b.dscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double h[3] = {0.0, 0.0, 0.0};
+  RET(cudaMemcpyAsync(h, b.ce_ss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RET(cudaMemcpyAsync(h + 1, b.dscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   RET(cudaStreamSynchronize(st));
-  *discarded = tot > 0.0 ? fmax(0.0, 1.0 - h[0] / tot) : 0.0;
-  *orth_defect = h[1];
+  const double tot = h[0];
+  *discarded = tot > 0.0 ? fmax(0.0, 1.0 - h[1] / tot) : 0.0;
+  *orth_defect = h[2];
   return cudaSuccess;
 }

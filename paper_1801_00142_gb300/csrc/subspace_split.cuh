@@ -20,10 +20,25 @@ struct SubspaceBuffers {
   __nv_bfloat16* pb;   // tensor-core operand planes (3 x 4cap x ld(4cap))
   long long psa, psb;  // their plane strides
   int* err;            // bounded-wait error flag of the tensor-core GEMM
+  // C_E as BF16 planes in both orientations and its squared Frobenius norm,
+  // written by reduce_partials_planes before subspace_split reads them
+  __nv_bfloat16* ce_rm;   // [plane][m][tc_ld(n)]
+  __nv_bfloat16* ce_tr;   // [plane][n][tc_ld(m)]
+  long long ce_ps;        // plane stride of both (elements)
+  double* ce_ss;          // ||C_E||_F^2 (device scalar)
+  // scaled CholeskyQR2: packed Cholesky factor, column scaling, 1 / L_jj,
+  // breakdown flag (0: the fast path succeeded)
+  float* chol_L;          // k (k + 1) / 2 with k <= 256
+  float* chol_d;          // 256
+  float* chol_li;         // 256
+  int* chol_flag;         // [0] breakdown flag of the current call, [1] count of breakdowns
 };
 
 // Largest k the orthonormalisation handles; wider splits take the exact path.
 constexpr int SUBSPACE_MAX_K = 256;
+
+// Floats of chol_L (k <= SUBSPACE_MAX_K).
+constexpr size_t SUBSPACE_CHOL_FLOATS = (size_t)256 * 257 / 2;
 
 // Orthonormalisations launched as one thread-block cluster (all contexts).
 extern unsigned long long g_orth_cluster_calls;
@@ -37,13 +52,15 @@ size_t subspace_buffer_floats(int cap);
 // CTAs of the orthonormalisation kernel for rows <= 4 cap.
 int subspace_orth_ctas(int cap);
 
-// Split C_E (m x n, FP64 row-major) into left (m x k) and right (k x n), FP64.
+// Split C_E (m x n) into left (m x k) and right (k x n), FP64.  C_E is read
+// from b.ce_rm / b.ce_tr / b.ce_ss (its planes and norm, see above); the
+// FP64 array CE itself is not read (the caller's exact fallback uses it).
 // dir_right = 1 (left-to-right): left = U orthonormal, right = U^T C_E,
 // warm = current C_{i+1} (kold x n, orthonormal rows).  dir_right = 0:
 // right = V^T orthonormal rows, left = C_E V, warm = current C_i (m x kold).
 // *orth_defect: max |Q^T Q - I| over the live columns of the orthonormal
 // factor; the caller falls back to the exact split when it is too large.
-// Synchronises the stream (reads FP64 norms).
+// Synchronises the stream once (reads the discarded weight and the defect).
 cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
                            const double* warm, int kold, double* left, double* right,
                            unsigned long long seed, const SubspaceBuffers& b, cudaStream_t st,

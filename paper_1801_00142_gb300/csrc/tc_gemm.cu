@@ -42,6 +42,8 @@ struct KParams {
   int pa_planes, pb_planes, nprod;
   int prod_a[6], prod_b[6];
   int a_batched, b_batched;
+  int a_mn, b_mn;   // operand staged MN-major (two 64-wide boxes per plane)
+  int m_fast;       // tile order: m fastest (fewer m tiles than n tiles) or n fastest
   int stages;
   int chunk_kb;   // K-blocks per main accumulation chunk
   TcOutput out;
@@ -105,10 +107,26 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128
-__host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
+// MN-major operand tile, 128-byte swizzle: K-rows of 64 contiguous MN
+// elements (128 B), 8-row atoms 1024 B apart along K (stride byte offset),
+// the two 64-wide MN halves of the 128-wide tile MN_HALF bytes apart
+// (leading byte offset).
+constexpr int MN_HALF = BK * 128;   // one half: 64 K-rows x 128 B
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(MN_HALF >> 4) << 16;    // leading byte offset: next 64 MN elements
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: next 8 K-rows
+  d |= (uint64_t)1 << 46;                 // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                 // swizzle mode: 128 B
+  return d;
+}
+
+// instruction descriptor: kind::f16, A = B = BF16, D = F32, M = 128, N = 128;
+// bits 15 / 16 select an MN-major A / B
+__host__ __device__ constexpr uint32_t idesc_bf16_128x128(int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a_mn & 1) << 15) |
+         ((uint32_t)(b_mn & 1) << 16) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -240,8 +258,25 @@ __device__ __forceinline__ void store_chunk(const TcOutput& o, long long om,
     if (jj < ncols) store_out(o, om + col[jj], v[jj]);
 }
 
+// Tile t -> (m tile, n tile, batch x split).  The smaller of the two output
+// dimensions runs fastest, so CTAs working at the same time share the tile
+// of the larger operand (read from DRAM once, then from L2).
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int m_fast, int& mt,
+                                            int& nt, int& z) {
+  const int mn = tiles_m * tiles_n;
+  z = t / mn;
+  const int r = t - z * mn;
+  if (m_fast) {
+    mt = r % tiles_m;
+    nt = r / tiles_m;
+  } else {
+    nt = r % tiles_n;
+    mt = r / tiles_n;
+  }
+}
+
 // Persistent kernel: every CTA walks the output tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ... (tile order: n fastest, then m, then batch x
+// blockIdx.x + gridDim.x, ... (tile order: see tile_coords, then batch x
 // split).  The main accumulator is double-buffered per chunk of chunk_kb
 // K-blocks and the corr accumulator per tile, so the MMAs of the next chunk
 // (and of the next tile) run while the epilogue drains and stores; the
@@ -301,7 +336,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     long long g = 0;   // k-blocks issued by this CTA
     bool ok = true;
     for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-      const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
+      int mt, nt, z;
+      tile_coords(t, tiles_m, tiles_n, p.m_fast, mt, nt, z);
       const int bidx = z / p.splitk, split = z % p.splitk;
       const int kb_begin = split * p.kb_per;
       const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
@@ -313,10 +349,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* st = smem + s * stage_bytes;
         mbar_expect_tx(&full[s], stage_bytes);
         const int k0 = kb * BK;
-        for (int q = 0; q < p.pa_planes; ++q)
-          tma_load_4d(st + q * TILE_BYTES, &mapA, &full[s], k0, mt * BM, ba, q);
-        for (int q = 0; q < p.pb_planes; ++q)
-          tma_load_4d(st + (p.pa_planes + q) * TILE_BYTES, &mapB, &full[s], k0, nt * BN, bb, q);
+        for (int q = 0; q < p.pa_planes; ++q) {
+          uint8_t* dst = st + q * TILE_BYTES;
+          if (p.a_mn) {
+            tma_load_4d(dst, &mapA, &full[s], mt * BM, k0, ba, q);
+            tma_load_4d(dst + MN_HALF, &mapA, &full[s], mt * BM + 64, k0, ba, q);
+          } else {
+            tma_load_4d(dst, &mapA, &full[s], k0, mt * BM, ba, q);
+          }
+        }
+        for (int q = 0; q < p.pb_planes; ++q) {
+          uint8_t* dst = st + (p.pa_planes + q) * TILE_BYTES;
+          if (p.b_mn) {
+            tma_load_4d(dst, &mapB, &full[s], nt * BN, k0, bb, q);
+            tma_load_4d(dst + MN_HALF, &mapB, &full[s], nt * BN + 64, k0, bb, q);
+          } else {
+            tma_load_4d(dst, &mapB, &full[s], k0, nt * BN, bb, q);
+          }
+        }
       }
     }
     // drain: every load issued must have landed before the CTA may exit
@@ -324,7 +374,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), p.err);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    const uint32_t idesc = idesc_bf16_128x128();
+    const uint32_t idesc = idesc_bf16_128x128(p.a_mn, p.b_mn);
     long long g = 0;   // k-blocks consumed (stage ring position)
     long long h = 0;   // main chunks issued
     int j = 0;         // tiles of this CTA
@@ -355,9 +405,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t dcol = pr == 0 ? mcol : ccol;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            // advance 16 BF16 = 32 B along K inside the swizzled 128-B row
-            uint64_t da = smem_desc(a_addr) + (uint64_t)(kk * 2);
-            uint64_t db = smem_desc(b_addr) + (uint64_t)(kk * 2);
+            // K-major: advance 16 BF16 = 32 B along K inside the swizzled
+            // 128-B row; MN-major: advance 16 K-rows = two 1024-B atoms
+            uint64_t da = p.a_mn ? smem_desc_mn(a_addr + kk * 2048) : smem_desc(a_addr) + (uint64_t)(kk * 2);
+            uint64_t db = p.b_mn ? smem_desc_mn(b_addr + kk * 2048) : smem_desc(b_addr) + (uint64_t)(kk * 2);
             const bool acc = pr == 0 ? (ci > 0 || kk > 0) : (kb > kb_begin || pr > 1 || kk > 0);
             mma_bf16(dcol, da, db, idesc, acc ? 1u : 0u);
           }
@@ -384,7 +435,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int j = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++j) {
-      const int nt = t % tiles_n, mt = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
+      int mt, nt, z;
+      tile_coords(t, tiles_m, tiles_n, p.m_fast, mt, nt, z);
       const int bidx = z / p.splitk, split = z % p.splitk;
       const int kb_begin = split * p.kb_per;
       const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
@@ -563,14 +615,19 @@ int chunk_kb() {
 cudaError_t make_map(CUtensorMap* map, const TcOperand& op) {
   EncodeFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
-  if (op.ld % 8 != 0 || op.ld < op.k || ((uintptr_t)op.base % 16) != 0) return cudaErrorInvalidValue;
-  const long long bstride = op.batches > 1 ? op.batch_stride : (long long)op.rows * op.ld;
-  cuuint64_t dims[4] = {(cuuint64_t)op.k, (cuuint64_t)op.rows, (cuuint64_t)op.batches,
+  if (op.ld % 8 != 0 || op.ld < (op.mn_major ? op.rows : op.k) || ((uintptr_t)op.base % 16) != 0)
+    return cudaErrorInvalidValue;
+  // K-major: (k, rows, batch, plane), box (64, 128); MN-major: (rows, k,
+  // batch, plane), box (64, 64), loaded twice per 128-wide tile
+  const long long outer = op.mn_major ? op.k : op.rows;
+  const long long bstride = op.batches > 1 ? op.batch_stride : outer * op.ld;
+  cuuint64_t dims[4] = {(cuuint64_t)(op.mn_major ? op.rows : op.k),
+                        (cuuint64_t)(op.mn_major ? op.k : op.rows), (cuuint64_t)op.batches,
                         (cuuint64_t)op.planes};
   cuuint64_t strides[3] = {(cuuint64_t)op.ld * 2, (cuuint64_t)bstride * 2,
                            (cuuint64_t)op.plane_stride * 2};
   if ((strides[1] % 16) || (strides[2] % 16)) return cudaErrorInvalidValue;
-  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)BM, 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)64, (cuuint32_t)(op.mn_major ? BK : BM), 1, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)op.base, dims, strides, box,
                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -604,6 +661,9 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   p.nprod = nprod;
   p.a_batched = A.batches > 1;
   p.b_batched = B.batches > 1;
+  p.a_mn = A.mn_major ? 1 : 0;
+  p.b_mn = B.mn_major ? 1 : 0;
+  p.m_fast = ((M + BM - 1) / BM) < ((N + BN - 1) / BN) ? 1 : 0;
   const int stage_bytes = (A.planes + B.planes) * TILE_BYTES;
   int S = (200 * 1024) / stage_bytes;
   if (S > 4) S = 4;

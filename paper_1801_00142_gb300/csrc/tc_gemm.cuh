@@ -2,8 +2,9 @@
 // accumulation in tensor memory), operands staged by TMA with 128-byte
 // swizzle, warp-specialised producer / MMA issuer / epilogue.
 //
-// Each operand is a K-major 4-D tensor [plane][batch][rows][k] of BF16 whose
-// planes hold a split x ~= x0 + x1 (+ x2) of a higher-precision value; the
+// Each operand is a 4-D tensor [plane][batch][rows][k] (K-major) or
+// [plane][batch][k][rows] (MN-major) of BF16 whose planes hold a split
+// x ~= x0 + x1 (+ x2) of a higher-precision value; the
 // product is accumulated as sum over the requested (plane_a, plane_b) pairs,
 // e.g. x0y0 + x0y1 + x1y0 (3 products, ~16 significant bits) or the six
 // products with plane index sum <= 2 (~24 bits).
@@ -23,10 +24,12 @@ struct TcOperand {
   const __nv_bfloat16* base;   // plane 0, batch 0, row 0, k 0
   int planes;
   int rows, k;                 // logical sizes (k is the contraction length)
-  long long ld;                // row stride in elements (multiple of 8)
+  long long ld;                // leading stride in elements (multiple of 8), see mn_major
   long long batch_stride;      // elements (0: operand shared by all batches)
   long long plane_stride;      // elements
   int batches;                 // 1 if shared
+  int mn_major = 0;            // 0: element (r, k) at r*ld + k (K-major);
+                               // 1: element (r, k) at k*ld + r (MN-major, rows contiguous)
 };
 
 struct TcOutput {

@@ -14,7 +14,9 @@
 struct TcGemmScratch {
   size_t a, b, part, total;
 };
-TcGemmScratch tc_gemm_scratch(int M, int N, int K, int batch, int planes, int splitk);
+// b_kn: B given as batch x K x N (C = A B) instead of batch x N x K (C = A B^T).
+TcGemmScratch tc_gemm_scratch(int M, int N, int K, int batch, int planes, int splitk,
+                              bool b_kn = false);
 
 // XTRG_EINVAL for arguments xtrg_tc_gemm rejects, else XTRG_OK.
 xtrg_status tc_gemm_check_args(const double* A, const double* B, double* C, int M, int N, int K,
@@ -23,4 +25,5 @@ xtrg_status tc_gemm_check_args(const double* A, const double* B, double* C, int 
 // C = A B^T on the tensor cores using the scratch at base (256-byte aligned,
 // tc_gemm_scratch(...).total bytes); synchronises st.
 xtrg_status tc_gemm_run(const double* A, const double* B, double* C, int M, int N, int K, int batch,
-                        int planes, int nprod, int splitk, char* base, cudaStream_t st);
+                        int planes, int nprod, int splitk, char* base, cudaStream_t st,
+                        bool b_kn = false);

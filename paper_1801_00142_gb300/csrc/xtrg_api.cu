@@ -47,10 +47,10 @@ struct DevMpo {
 struct Plan {
   int L, DH, cap, cap_fat, fat_bond, capc;
   size_t n_h, n_site, n_csite, n_fat, n_pp, n_env, n_part, n_ce, n_svd, n_svd_cols, n_usbuf,
-      n_obs;
+      n_obs, n_herm;
   // tensor-core path (per plane, in BF16 elements)
   int planes;
-  size_t m_site[4], m_env, m_t1, m_lp, m_lpt, m_ct, m_part;
+  size_t m_site[4], m_env, m_t1, m_lp, m_ct, m_part;
   size_t mixed_bytes;
   size_t total;
 };
@@ -87,6 +87,7 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
   p->n_svd_cols = 4 * capc;
   p->n_usbuf = capc * capc;
   p->n_obs = (size_t)DH * DH * 4 * cap * 2;
+  p->n_herm = cap * cap;   // one transfer matrix of the Hermiticity check (T: 4 of these)
   p->planes = cfg->prec == XTRG_BF16X6 ? 3 : 2;
   {
     const size_t c = cap, l1 = tc_ld(c), l2 = tc_ld(2 * c), lsq = tc_ld(c * c), l4 = tc_ld(4 * c);
@@ -97,7 +98,6 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
     p->m_env = c * c * l1;
     p->m_t1 = c * 2 * c * l2;
     p->m_lp = 4 * c * lsq;
-    p->m_lpt = c * c * l4;
     p->m_ct = c * l4;
     p->m_part = (size_t)SPLITK_MAX * 16 * c * c;
     size_t pl = p->planes, mb = 0;
@@ -106,10 +106,12 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
     // the halves of the two-site environment: one of each, or one per site
     // when they stay resident (keep_parts)
     const size_t nparts = cfg->keep_parts ? (size_t)L : 1;
-    mb += 2 * up(pl * p->m_t1 * 2) + 2 * up(nparts * pl * p->m_lp * 2) + 2 * up(pl * p->m_lpt * 2);
+    mb += 2 * up(pl * p->m_t1 * 2) + 2 * up(nparts * pl * p->m_lp * 2);
     mb += up(pl * p->m_ct * 2) + up(p->m_part * 4) + ALIGN;
     mb += up(subspace_buffer_floats(p->cap) * 4) + 3 * ALIGN;
     mb += up(subspace_plane_elems_a(p->cap) * 2) + up(subspace_plane_elems_b(p->cap) * 2);
+    mb += 2 * up(subspace_plane_elems_a(p->cap) * 2) + ALIGN;   // C_E planes, both orientations
+    mb += up(SUBSPACE_CHOL_FLOATS * 4) + 2 * up(256 * 4) + ALIGN;   // CholeskyQR2 factor
     p->mixed_bytes = (cfg->prec == XTRG_FP64) ? 0 : mb;
   }
   size_t t = 0;
@@ -125,6 +127,7 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
   t += 2 * up(p->n_svd * 8) + up(p->n_svd_cols * 8) + up(p->n_svd_cols * 4) + 3 * ALIGN;
   t += up(p->n_usbuf * 8);
   t += 3 * up(p->n_obs * 8);
+  t += 8 * up(p->n_herm * 8);              // Hermiticity transfers: 2 + 2 ping-pong, T (x4)
   t += up(64 * 8);                          // scalars
   t += p->mixed_bytes;
   p->total = t;
@@ -140,11 +143,13 @@ struct xtrg_ctx {
   xtrg_config cfg{};
   Plan plan{};
   int L = 0, DH = 0, cap = 0;
+  int sms = 152;   // SMs of the device the context was created on
   DevMpo H, rho, C, Y, I, fat;
   double* pp[2] = {nullptr, nullptr};
   std::vector<double*> env;
   double *T1 = nullptr, *Lp = nullptr, *Rp = nullptr, *CE = nullptr, *usbuf = nullptr;
   double *ob[3] = {nullptr, nullptr, nullptr};
+  double *hf[2] = {nullptr, nullptr}, *hr[2] = {nullptr, nullptr}, *ht = nullptr;
   double* scal = nullptr;
   SvdBuffers svd{};
   // tensor-core path buffers (BF16 planes)
@@ -152,8 +157,7 @@ struct xtrg_ctx {
     int P = 0, nprod = 0;
     std::vector<__nv_bfloat16*> site[4];
     std::vector<__nv_bfloat16*> env;
-    __nv_bfloat16 *T1 = nullptr, *T1R = nullptr, *Lp = nullptr, *Rp = nullptr, *LpT = nullptr,
-                  *RpT = nullptr, *Ct = nullptr;
+    __nv_bfloat16 *T1 = nullptr, *T1R = nullptr, *Lp = nullptr, *Rp = nullptr, *Ct = nullptr;
     // left half of site i / right half of site j (distinct buffers per site
     // when keep_parts, else all alias Lp / Rp)
     std::vector<__nv_bfloat16*> lpc, rpc;
@@ -355,6 +359,57 @@ xtrg_status right_env(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, const Dev
                       0));
 }
 
+#define CKM(x)                                                                              \
+  do {                                                                                      \
+    cudaError_t _e = (x);                                                                   \
+    if (_e != cudaSuccess)                                                                  \
+      return fail(ctx, XTRG_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #x,                  \
+                  cudaGetErrorString(_e));                                                  \
+  } while (0)
+
+// Profiling: a pair of events around a stretch of stream work, tagged with
+// its call site (tags 0-4: tensor-core GEMMs, 5: truncation of the
+// tensor-core path, 6: one FP64 two-site update, 7: the FP64 initial right
+// environments); the first is recorded here, the second by the caller after
+// the work.
+constexpr int TAG_SPLIT = 5, TAG_UPDATE64 = 6, TAG_ENVPASS64 = 7;
+xtrg_status ev_pair(xtrg_ctx* ctx, int tag, cudaEvent_t* e0, cudaEvent_t* e1) {
+  if (ctx->ev_used + 2 > ctx->ev.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      CKM(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+  }
+  *e0 = ctx->ev[ctx->ev_used++];
+  *e1 = ctx->ev[ctx->ev_used++];
+  ctx->ev_tag.push_back(tag);
+  ctx->tag_n[tag]++;
+  CKM(cudaEventRecord(*e0, ctx->st));
+  return XTRG_OK;
+}
+
+// sum the recorded event intervals by tag (the stream has been synchronised)
+xtrg_status resolve_events(xtrg_ctx* ctx) {
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float ms = 0.f;
+    // a pair left open by a call that failed midway is skipped
+    if (cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const int tag = i / 2 < ctx->ev_tag.size() ? ctx->ev_tag[i / 2] : 0;
+    if (tag == TAG_SPLIT)
+      ctx->split_ms += ms;
+    else
+      ctx->tc_ms += ms;
+    ctx->tag_ms[tag] += ms;
+  }
+  ctx->ev_used = 0;
+  ctx->ev_tag.clear();
+  return XTRG_OK;
+}
+
 // Variational compression of A^T B into C (App. D.1).  C holds the guess,
 // already right-canonical; on return C is the compressed MPO with its
 // orthogonality centre at site 0.
@@ -364,16 +419,21 @@ xtrg_status compress(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, DevMpo& C,
   const int kcap = dstar < ctx->cap ? dstar : ctx->cap;
   CK(dev_fill(ctx->env[0], 1.0, 1, ctx->st));
   CK(dev_fill(ctx->env[L], 1.0, 1, ctx->st));
+  cudaEvent_t p0 = nullptr, p1 = nullptr;
+  if (ctx->profiling) TRY(ev_pair(ctx, TAG_ENVPASS64, &p0, &p1));
   for (int j = L - 1; j >= 1; --j) {
     TRY(right_part(ctx, A, B, C, j, ctx->env[j + 1]));
     TRY(right_env(ctx, A, B, C, j, ctx->env[j]));
   }
+  if (p1) CK(cudaEventRecord(p1, ctx->st));
   double maxdisc = 0.0;
   for (int s = 0; s < sweeps; ++s) {
     const bool last = s == sweeps - 1;
     for (int dir = 0; dir < 2; ++dir) {
       for (int step = 0; step < L - 1; ++step) {
         const int i = dir == 0 ? step : L - 2 - step;
+        cudaEvent_t u0 = nullptr, u1 = nullptr;
+        if (ctx->profiling) TRY(ev_pair(ctx, TAG_UPDATE64, &u0, &u1));
         TRY(left_part(ctx, A, B, C, i, ctx->env[i]));
         TRY(right_part(ctx, A, B, C, i + 1, ctx->env[i + 2]));
         const int m = 4 * C.dims[i], n = 4 * C.dims[i + 2];
@@ -387,9 +447,14 @@ xtrg_status compress(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, DevMpo& C,
         if (last && r.discarded > maxdisc) maxdisc = r.discarded;
         if (dir == 0) TRY(left_env(ctx, A, B, C, i, ctx->env[i + 1]));
         else TRY(right_env(ctx, A, B, C, i + 1, ctx->env[i + 1]));
+        if (u1) CK(cudaEventRecord(u1, ctx->st));
         ctx->updates++;
       }
     }
+  }
+  if (ctx->profiling) {
+    CK(cudaStreamSynchronize(ctx->st));
+    TRY(resolve_events(ctx));
   }
   ctx->last_trunc = maxdisc;
   return XTRG_OK;
@@ -443,7 +508,8 @@ bool mixed_for_beta(const xtrg_ctx* ctx, double beta) {
 //   environment  V[c][b][a]                 (left and right alike)
 //   left half    T1[c][(s,a')][(b,t)]  ->  Lp[(c,s,u)][(b',a')]
 //   right half   T1R[c''][(a',s')][(t',b'')]  ->  Rp[(s',u',c'')][(b',a')]
-//   C_E = Lp Rp^T (split-K, FP64 sum); env update V' = C^T-part x (Lp or Rp)^T.
+//   C_E = Lp Rp^T (split-K, FP64 sum); env update V' = C^T-part x (Lp or Rp)
+//   with the half read MN-major.
 
 TcOperand opnd(const __nv_bfloat16* base, int P, int rows, int k, long long ld,
                long long batch_stride, long long plane_stride, int batches) {
@@ -459,34 +525,6 @@ TcOutput out_planes(__nv_bfloat16* base, int P, long long ps, Idx3 cm, Idx3 cn, 
   o.mode = TC_OUT_BF16P; o.bf16 = base; o.planes = P; o.plane_stride = ps;
   o.cm = cm; o.cn = cn; o.scb = scb; o.alpha = 1.0;
   return o;
-}
-
-#define CKM(x)                                                                              \
-  do {                                                                                      \
-    cudaError_t _e = (x);                                                                   \
-    if (_e != cudaSuccess)                                                                  \
-      return fail(ctx, XTRG_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #x,                  \
-                  cudaGetErrorString(_e));                                                  \
-  } while (0)
-
-// Profiling: a pair of events around a stretch of stream work, tagged with
-// its call site (tags 0-4: tensor-core GEMMs, 5: truncation); the first is
-// recorded here, the second by the caller after the work.
-constexpr int TAG_SPLIT = 5;
-xtrg_status ev_pair(xtrg_ctx* ctx, int tag, cudaEvent_t* e0, cudaEvent_t* e1) {
-  if (ctx->ev_used + 2 > ctx->ev.size()) {
-    for (int i = 0; i < 256; ++i) {
-      cudaEvent_t e;
-      CKM(cudaEventCreate(&e));
-      ctx->ev.push_back(e);
-    }
-  }
-  *e0 = ctx->ev[ctx->ev_used++];
-  *e1 = ctx->ev[ctx->ev_used++];
-  ctx->ev_tag.push_back(tag);
-  ctx->tag_n[tag]++;
-  CKM(cudaEventRecord(*e0, ctx->st));
-  return XTRG_OK;
 }
 
 xtrg_status tc(xtrg_ctx* ctx, const TcOperand& A, const TcOperand& B, int M, int N, int K,
@@ -507,26 +545,6 @@ xtrg_status tc(xtrg_ctx* ctx, const TcOperand& A, const TcOperand& B, int M, int
   return XTRG_OK;
 }
 
-// sum the recorded tensor-core GEMM intervals (the stream has been synchronised)
-xtrg_status resolve_events(xtrg_ctx* ctx) {
-  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
-    float ms = 0.f;
-    // a pair left open by a call that failed midway is skipped
-    if (cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    const int tag = i / 2 < ctx->ev_tag.size() ? ctx->ev_tag[i / 2] : 0;
-    if (tag == TAG_SPLIT)
-      ctx->split_ms += ms;
-    else
-      ctx->tc_ms += ms;
-    ctx->tag_ms[tag] += ms;
-  }
-  ctx->ev_used = 0;
-  ctx->ev_tag.clear();
-  return XTRG_OK;
-}
 
 // BF16-plane copies of rho's sites for the four substep layouts.
 xtrg_status mixed_prepare(xtrg_ctx* ctx) {
@@ -612,12 +630,12 @@ xtrg_status mixed_env(xtrg_ctx* ctx, const double* Csite, int kout, int kin, boo
   // C^T-part [c'][k]: left reads C_i[k][c'], right reads C_j[c'][k]
   CKM(to_planes(Csite, left ? idx_plain(1) : idx_plain(kin), left ? idx_plain(kout) : idx_plain(1),
                 0, kout, kin, 1, ctx->m.Ct, ldK, 0, P, ctx->plan.m_ct, ctx->st));
-  __nv_bfloat16* T = left ? ctx->m.LpT : ctx->m.RpT;
-  CKM(transpose_planes(part, ldP, (int)ab, kin, T, ldK, P, ctx->plan.m_lp, ctx->plan.m_lpt,
-                       ctx->st));
   ctx->cur_tag = 4;
   TcOperand Ac = opnd(ctx->m.Ct, P, kout, kin, ldK, 0, ctx->plan.m_ct, 1);
-  TcOperand Bt = opnd(T, P, (int)ab, kin, ldK, 0, ctx->plan.m_lpt, 1);
+  // B(n = (b',a'), k = (c,s,u)) is the half itself, [k][n] with row stride
+  // ldP: staged MN-major, no transpose pass
+  TcOperand Bt = opnd(part, P, (int)ab, kin, ldP, 0, ctx->plan.m_lp, 1);
+  Bt.mn_major = 1;
   return tc(ctx, Ac, Bt, kout, (int)ab, kin, 1, 1,
             out_planes(ctx->m.env[slot], P, ctx->plan.m_env, idx_plain((long long)a * ldE),
                        idx_split2(a, ldE, 1), 0));
@@ -630,14 +648,27 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, const __nv_bfloat16* Lp, const __nv_bfloat16
   const long long K = (long long)a2 * a2, ld = tc_ld(K);
   const int kb = (int)((K + 63) / 64);
   const int tiles = ((m + 127) / 128) * ((n + 127) / 128);
-  // enough splits to fill the GPU twice over, and each FP32 accumulation
-  // chain at most 32 K-blocks (2048 terms) long; the partials are summed in FP64
-  int splitk = (2 * 152 + tiles - 1) / tiles;
-  const int by_len = (kb + 31) / 32;
-  if (splitk < by_len) splitk = by_len;
-  if (splitk > SPLITK_MAX) splitk = SPLITK_MAX;
-  if (splitk > kb / 4) splitk = kb / 4;
-  if (splitk < 1) splitk = 1;
+  // split-K only to fill the persistent CTAs (the kernel's accumulation is
+  // unbiased at any chain length): the fewest splits whose work units fill
+  // their waves over the SMs to >= 95 %, each split keeping >= 4 K-blocks;
+  // the FP32 partials are summed in FP64
+  const int sms = ctx->sms;
+  int splitk = 1;
+  {
+    int best = 1;
+    double best_eff = 0.0;
+    for (int s = 1; s <= SPLITK_MAX && s <= kb / 4; ++s) {
+      const long long units = (long long)tiles * s;
+      const long long waves = (units + sms - 1) / sms;
+      const double eff = (double)units / (double)(waves * sms);
+      if (eff > best_eff + 1e-9) {
+        best = s;
+        best_eff = eff;
+      }
+      if (eff >= 0.95) break;
+    }
+    splitk = best;
+  }
   ctx->cur_tag = 3;
   TcOperand Al = opnd(Lp, P, m, (int)K, ld, 0, ctx->plan.m_lp, 1);
   TcOperand Br = opnd(Rp, P, n, (int)K, ld, 0, ctx->plan.m_lp, 1);
@@ -645,7 +676,11 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, const __nv_bfloat16* Lp, const __nv_bfloat16
   memset(&o, 0, sizeof o);
   o.mode = TC_OUT_PARTIAL; o.f32 = ctx->m.part; o.alpha = 1.0;
   TRY(tc(ctx, Al, Br, m, n, (int)K, 1, splitk, o));
-  CKM(reduce_partials(ctx->m.part, splitk, (long long)m * n, ctx->CE, ctx->st));
+  // FP64 C_E (exact fallback, debug scans), its planes in both orientations
+  // for the subspace products and ||C_E||^2, in one pass over the partials
+  CKM(reduce_partials_planes(ctx->m.part, splitk, m, n, ctx->CE, ctx->m.sb.ce_rm, tc_ld(n),
+                             ctx->m.sb.ce_tr, tc_ld(m), ctx->m.sb.ce_ps, ctx->m.sb.ce_ss,
+                             ctx->st));
   return XTRG_OK;
 }
 
@@ -781,6 +816,41 @@ xtrg_status traces(xtrg_ctx* ctx, bool want_h, double out[3]) {
   return XTRG_OK;
 }
 
+// ||rho||_F^2 = sum rho_{s,t} rho_{s,t} and Tr(rho rho) = sum rho_{s,t} rho_{t,s}
+// by left-to-right transfer matrices E[l][m] (FP64).  Both share the first
+// contraction of each site, T[m][s][t][x] = sum_l E[l][m] rho[l][s][t][x];
+// the second pairs T with rho[m][s][t][y] (Frobenius) or rho[m][t][s][y]
+// (the transpose on the physical pair).  Their difference is the
+// Hermiticity defect ||rho - rho^T||_F^2 = 2 (||rho||_F^2 - Tr(rho rho))
+// of a real rho (Sec. II B: rho^T rho is the positivity-preserving product).
+xtrg_status herm_transfers(xtrg_ctx* ctx, double* fro, double* trr) {
+  const int L = ctx->L;
+  const DevMpo& R = ctx->rho;
+  double* T = ctx->ht;
+  CK(dev_fill(ctx->hf[0], 1.0, 1, ctx->st));
+  CK(dev_fill(ctx->hr[0], 1.0, 1, ctx->st));
+  for (int i = 0; i < L; ++i) {
+    const int l = R.dims[i], r = R.dims[i + 1];
+    double* Ef = ctx->hf[i & 1];
+    double* Er = ctx->hr[i & 1];
+    for (int which = 0; which < 2; ++which) {
+      const double* E = which == 0 ? Ef : Er;
+      double* En = which == 0 ? ctx->hf[(i + 1) & 1] : ctx->hr[(i + 1) & 1];
+      // T[m][(s,t,x)] = sum_l E[l][m] rho[l][(s,t,x)]
+      TRY(gemm64(ctx, mk(l, 4 * r, l, 1, E, idx_plain(1), idx_plain(l), 0, R.site[i],
+                         idx_plain(4 * r), idx_plain(1), 0, T, idx_plain(4 * r), idx_plain(1), 0)));
+      // E'[x][y] = sum_{(m,s,t)} T[(m,s,t)][x] rho[m][s or t][t or s][y]
+      const Idx3 bk = which == 0 ? idx_plain(r) : idx_split3(2, 2, 4LL * r, r, 2LL * r);
+      TRY(gemm64(ctx, mk(r, r, 4 * l, 1, T, idx_plain(1), idx_plain(r), 0, R.site[i], bk,
+                         idx_plain(1), 0, En, idx_plain(r), idx_plain(1), 0)));
+    }
+  }
+  CK(cudaMemcpyAsync(fro, ctx->hf[L & 1], sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(trr, ctx->hr[L & 1], sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return XTRG_OK;
+}
+
 xtrg_status check_mpo(const xtrg_mpo* m, int cap_bond) {
   if (!m || m->L < 2 || m->d != 2 || !m->bond_dims || !m->W) return XTRG_EINVAL;
   if (m->bond_dims[0] != 1 || m->bond_dims[m->L] != 1) return XTRG_EINVAL;
@@ -831,6 +901,12 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   ctx->L = Hm->L;
   ctx->DH = p.DH;
   ctx->cap = p.cap;
+  {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      ctx->sms = n;
+  }
   bool ok = carve_mpo(ctx, &ctx->H, p.n_h) && carve_mpo(ctx, &ctx->I, 4) &&
             carve_mpo(ctx, &ctx->rho, p.n_csite) && carve_mpo(ctx, &ctx->C, p.n_csite) &&
             carve_mpo(ctx, &ctx->Y, p.n_site) && carve_mpo(ctx, &ctx->fat, p.n_fat);
@@ -852,10 +928,16 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   ctx->svd.max_cols = (int)p.n_svd_cols;
   ctx->usbuf = (double*)carve(ctx, p.n_usbuf * 8);
   for (int i = 0; i < 3; ++i) ctx->ob[i] = (double*)carve(ctx, p.n_obs * 8);
+  for (int i = 0; i < 2; ++i) {
+    ctx->hf[i] = (double*)carve(ctx, p.n_herm * 8);
+    ctx->hr[i] = (double*)carve(ctx, p.n_herm * 8);
+  }
+  ctx->ht = (double*)carve(ctx, 4 * p.n_herm * 8);
   ctx->scal = (double*)carve(ctx, 64 * 8);
   ok = ok && envbase && ctx->pp[0] && ctx->pp[1] && ctx->T1 && ctx->Lp && ctx->Rp && ctx->CE &&
        ctx->svd.W && ctx->svd.V && ctx->svd.sig && ctx->svd.perm && ctx->svd.counter &&
        ctx->svd.kept && ctx->svd.stats && ctx->usbuf && ctx->ob[0] && ctx->ob[1] && ctx->ob[2] &&
+       ctx->hf[0] && ctx->hf[1] && ctx->hr[0] && ctx->hr[1] && ctx->ht &&
        ctx->scal;
   if (ok && p.mixed_bytes) {
     const int P = p.planes, L = ctx->L;
@@ -881,8 +963,6 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
         ctx->m.rpc.push_back(ctx->m.Rp + o);
       }
     }
-    ctx->m.LpT = (__nv_bfloat16*)carve(ctx, P * p.m_lpt * 2);
-    ctx->m.RpT = (__nv_bfloat16*)carve(ctx, P * p.m_lpt * 2);
     ctx->m.Ct = (__nv_bfloat16*)carve(ctx, P * p.m_ct * 2);
     ctx->m.part = (float*)carve(ctx, p.m_part * 4);
     ctx->m.err = (int*)carve(ctx, 16);
@@ -910,10 +990,21 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
       ctx->m.sb.psa = (long long)(subspace_plane_elems_a(p.cap) / 3);
       ctx->m.sb.psb = (long long)(subspace_plane_elems_b(p.cap) / 3);
       ctx->m.sb.err = ctx->m.err;
+      ctx->m.sb.ce_ps = (long long)(subspace_plane_elems_a(p.cap) / 3);
+      ctx->m.sb.ce_rm = (__nv_bfloat16*)carve(ctx, subspace_plane_elems_a(p.cap) * 2);
+      ctx->m.sb.ce_tr = (__nv_bfloat16*)carve(ctx, subspace_plane_elems_a(p.cap) * 2);
+      ctx->m.sb.ce_ss = (double*)carve(ctx, 16);
+      ctx->m.sb.chol_L = (float*)carve(ctx, SUBSPACE_CHOL_FLOATS * 4);
+      ctx->m.sb.chol_d = (float*)carve(ctx, 256 * 4);
+      ctx->m.sb.chol_li = (float*)carve(ctx, 256 * 4);
+      ctx->m.sb.chol_flag = (int*)carve(ctx, 16);
+      ok = ok && ctx->m.sb.ce_rm && ctx->m.sb.ce_tr && ctx->m.sb.ce_ss && ctx->m.sb.chol_L &&
+           ctx->m.sb.chol_d && ctx->m.sb.chol_li && ctx->m.sb.chol_flag;
+      if (ok && cudaMemsetAsync(ctx->m.sb.chol_flag, 0, 16, ctx->st) != cudaSuccess) ok = false;
       ok = ok && ctx->m.sb.dscal && ctx->m.sb.pa && ctx->m.sb.pb;
     }
-    ok = ok && ctx->m.T1 && ctx->m.T1R && ctx->m.Lp && ctx->m.Rp && ctx->m.LpT && ctx->m.RpT &&
-         ctx->m.Ct && ctx->m.part && ctx->m.err;
+    ok = ok && ctx->m.T1 && ctx->m.T1R && ctx->m.Lp && ctx->m.Rp && ctx->m.Ct && ctx->m.part &&
+         ctx->m.err;
     ctx->mixed_ready = ok;
   }
   if (!ok) {
@@ -1045,11 +1136,70 @@ extern "C" xtrg_status xtrg_observables(xtrg_ctx* ctx, xtrg_obs* o) {
   // the stored rho is normalised, ||rho||_F = 1, so Z(2 beta) = e^{2 ln c}
   o->lnZ2 = 2.0 * ctx->lnc;
   o->trunc_err = ctx->last_trunc;
-  o->herm_defect = 0.0;
+  double fro = 0.0, trr = 0.0;
+  TRY(herm_transfers(ctx, &fro, &trr));
+  if (!(fro > 0.0) || !std::isfinite(fro) || !std::isfinite(trr))
+    return fail(ctx, XTRG_ENUMERIC, "||rho||_F^2 = %g, Tr(rho rho) = %g", fro, trr);
+  o->herm_defect = std::sqrt(std::fmax(0.0, 2.0 - 2.0 * trr / fro));
   int mx = 1;
   for (int d : ctx->rho.dims) mx = d > mx ? d : mx;
   o->max_bond = mx;
   o->n_doublings = ctx->nd;
+  return XTRG_OK;
+}
+
+// MPO entanglement per bond (Sec. IV A, Eq. purif): rho read as a state of
+// the doubled local space; its Schmidt values s at each bond give
+// p = s^2 / sum s^2 and S_E = -sum p ln p.  A copy of rho brought to
+// right-canonical form in FP64 (into C, the scratch MPO of the products) is
+// swept left to right: the
+// centre site (l s t) x r is split by the FP64 Jacobi SVD, U stays, Lambda V^T
+// moves into the next site, and the singular values of each split are the
+// Schmidt values of that bond.  Nothing is truncated.
+extern "C" xtrg_status xtrg_entanglement(xtrg_ctx* ctx, double* S, int n) {
+  if (!ctx || !S) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "no state");
+  const int L = ctx->L;
+  if (n < L - 1) return fail(ctx, XTRG_EINVAL, "S holds %d entries, %d bonds", n, L - 1);
+  DevMpo& C = ctx->C;
+  // always an FP64 right-canonical form: a state from the tensor-core path is
+  // right-orthonormal only to FP32 level, which would bias the Schmidt values
+  TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, C));
+  std::vector<double> sig;
+  for (int i = 0; i + 1 < L; ++i) {
+    const int l = C.dims[i], r = C.dims[i + 1], r2 = C.dims[i + 2];
+    SvdResult res;
+    // keep every nonzero singular value (rel_tol 0): the next site absorbs Lambda V^T
+    bool conv = true;
+    cudaError_t e = svd_split_f64(C.site[i], 4 * l, r, r, 0.0, SPLIT_RIGHT, ctx->pp[0], ctx->usbuf,
+                                  ctx->svd, ctx->st, &res, &conv);
+    if (e == cudaErrorLaunchTimeout)
+      return fail(ctx, XTRG_ETIMEOUT, "entanglement split: a bounded device barrier expired");
+    if (e != cudaSuccess) return fail(ctx, XTRG_ECUDA, "entanglement split: %s", cudaGetErrorString(e));
+    if (!conv) return fail(ctx, XTRG_ENUMERIC, "Jacobi SVD at bond %d did not converge", i + 1);
+    const int ncols = (4 * l < r) ? 4 * l : r;
+    sig.resize(ncols);
+    CK(cudaMemcpyAsync(sig.data(), ctx->svd.sig, sizeof(double) * ncols, cudaMemcpyDeviceToHost,
+                       ctx->st));
+    // site i+1 <- (Lambda V^T) (k x r) times site i+1 (r x 4 r2)
+    const int k = res.k;
+    TRY(gemm64(ctx, mk(k, 4 * r2, r, 1, ctx->usbuf, idx_plain(r), idx_plain(1), 0, C.site[i + 1],
+                       idx_plain(4 * r2), idx_plain(1), 0, ctx->pp[1], idx_plain(4 * r2),
+                       idx_plain(1), 0)));
+    CK(cudaMemcpyAsync(C.site[i + 1], ctx->pp[1], sizeof(double) * (size_t)k * 4 * r2,
+                       cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    C.dims[i + 1] = k;
+    double tot = 0.0;
+    for (double x : sig) tot += x * x;
+    double ent = 0.0;
+    if (tot > 0.0)
+      for (double x : sig) {
+        const double p = x * x / tot;
+        if (p > 0.0) ent -= p * std::log(p);
+      }
+    S[i] = ent;
+  }
   return XTRG_OK;
 }
 
@@ -1089,6 +1239,87 @@ extern "C" xtrg_status xtrg_set_state(xtrg_ctx* ctx, const xtrg_mpo* r, double l
   return XTRG_OK;
 }
 
+// ------------------------------------------------------------ checkpoints
+// Device checkpoint layout: a 4 KiB header (magic, L, bond dims, ln c, beta,
+// doublings, canonical flag) followed by the sites packed back to back.
+namespace {
+constexpr long long CKPT_MAGIC = 0x58545247434b5054LL;   // "XTRGCKPT"
+constexpr size_t CKPT_HEADER = 4096;
+struct CkptHeader {
+  long long magic;
+  int L, nd, canonical, pad;
+  double lnc, beta;
+  int dims[(CKPT_HEADER - 40) / sizeof(int)];
+};
+static_assert(sizeof(CkptHeader) <= CKPT_HEADER, "checkpoint header");
+}  // namespace
+
+extern "C" size_t xtrg_checkpoint_bytes(const xtrg_ctx* ctx) {
+  if (!ctx || ctx->L + 1 > (int)((CKPT_HEADER - 40) / sizeof(int))) return 0;
+  return CKPT_HEADER + up((size_t)ctx->L * ctx->cap * 4 * ctx->cap * 8);
+}
+
+extern "C" xtrg_status xtrg_checkpoint_save(xtrg_ctx* ctx, void* dev_buf, size_t bytes) {
+  if (!ctx || !dev_buf || ((uintptr_t)dev_buf % ALIGN) != 0) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "no state to checkpoint");
+  const size_t need = xtrg_checkpoint_bytes(ctx);
+  if (need == 0 || bytes < need) return fail(ctx, XTRG_ENOMEM, "checkpoint buffer below %zu bytes", need);
+  CkptHeader h;
+  memset(&h, 0, sizeof h);
+  h.magic = CKPT_MAGIC;
+  h.L = ctx->L;
+  h.nd = ctx->nd;
+  h.canonical = ctx->rho_canonical ? 1 : 0;
+  h.lnc = ctx->lnc;
+  h.beta = ctx->beta;
+  for (int i = 0; i <= ctx->L; ++i) h.dims[i] = ctx->rho.dims[i];
+  char* d = (char*)dev_buf;
+  CK(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, ctx->st));
+  size_t off = CKPT_HEADER;
+  for (int i = 0; i < ctx->L; ++i) {
+    const size_t b = sizeof(double) * site_elems(ctx->rho, i);
+    CK(cudaMemcpyAsync(d + off, ctx->rho.site[i], b, cudaMemcpyDeviceToDevice, ctx->st));
+    off += b;
+  }
+  // the header is copied from this stack frame: finish before returning
+  CK(cudaStreamSynchronize(ctx->st));
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_checkpoint_load(xtrg_ctx* ctx, const void* dev_buf, size_t bytes) {
+  if (!ctx || !dev_buf || ((uintptr_t)dev_buf % ALIGN) != 0) return XTRG_EINVAL;
+  if (bytes < CKPT_HEADER) return fail(ctx, XTRG_EINVAL, "checkpoint buffer too small");
+  CkptHeader h;
+  const char* d = (const char*)dev_buf;
+  CK(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (h.magic != CKPT_MAGIC || h.L != ctx->L)
+    return fail(ctx, XTRG_EINVAL, "not a checkpoint of a %d-site context", ctx->L);
+  if (h.dims[0] != 1 || h.dims[h.L] != 1)
+    return fail(ctx, XTRG_EINVAL, "checkpoint has bad boundary bonds");
+  size_t need = CKPT_HEADER;
+  for (int i = 0; i < h.L; ++i) {
+    if (h.dims[i + 1] < 1 || h.dims[i + 1] > ctx->cap)
+      return fail(ctx, XTRG_EINVAL, "checkpoint bond %d = %d exceeds capacity %d", i + 1,
+                  h.dims[i + 1], ctx->cap);
+    need += sizeof(double) * (size_t)h.dims[i] * 4 * h.dims[i + 1];
+  }
+  if (bytes < need) return fail(ctx, XTRG_EINVAL, "checkpoint buffer shorter than its sites");
+  for (int i = 0; i <= ctx->L; ++i) ctx->rho.dims[i] = h.dims[i];
+  size_t off = CKPT_HEADER;
+  for (int i = 0; i < ctx->L; ++i) {
+    const size_t b = sizeof(double) * site_elems(ctx->rho, i);
+    CK(cudaMemcpyAsync(ctx->rho.site[i], d + off, b, cudaMemcpyDeviceToDevice, ctx->st));
+    off += b;
+  }
+  ctx->lnc = h.lnc;
+  ctx->beta = h.beta;
+  ctx->nd = h.nd;
+  ctx->have_rho = true;
+  ctx->rho_canonical = h.canonical != 0;
+  return XTRG_OK;
+}
+
 extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
   if (!ctx || !o) return XTRG_EINVAL;
   o->contraction_flops = ctx->flops_contr;
@@ -1101,6 +1332,18 @@ extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
   o->exact_split_fallbacks = ctx->fallbacks;
   o->split_ms = ctx->split_ms;
   o->orth_cluster_calls = (long long)__atomic_load_n(&g_orth_cluster_calls, __ATOMIC_RELAXED);
+  o->orth_fallbacks = 0;
+  if (ctx->mixed_ready && ctx->m.sb.chol_flag) {
+    int h[2] = {0, 0};
+    if (cudaMemcpyAsync(h, ctx->m.sb.chol_flag, sizeof h, cudaMemcpyDeviceToHost, ctx->st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess)
+      return XTRG_ECUDA;
+    o->orth_fallbacks = h[1];
+  }
+  o->fp64_update_ms = ctx->tag_ms[TAG_UPDATE64];
+  o->fp64_updates_timed = ctx->tag_n[TAG_UPDATE64];
+  o->fp64_env_pass_ms = ctx->tag_ms[TAG_ENVPASS64];
   return XTRG_OK;
 }
 
@@ -1113,11 +1356,12 @@ extern "C" xtrg_status xtrg_set_profiling(xtrg_ctx* ctx, int on) {
 // Layout of the scratch of one FP64 tensor-core GEMM call (shared by the
 // workspace and the static-scratch entry points): A planes, B planes, split-K
 // partials, error flag.
-TcGemmScratch tc_gemm_scratch(int M, int N, int K, int batch, int planes, int splitk) {
+TcGemmScratch tc_gemm_scratch(int M, int N, int K, int batch, int planes, int splitk, bool b_kn) {
   TcGemmScratch w;
   const size_t ld = (size_t)tc_ld(K);
   w.a = up((size_t)planes * batch * M * ld * 2);
-  w.b = up((size_t)planes * batch * N * ld * 2);
+  w.b = b_kn ? up((size_t)planes * batch * K * tc_ld(N) * 2)
+             : up((size_t)planes * batch * N * ld * 2);
   w.part = up((size_t)splitk * batch * M * N * 4);
   w.total = w.a + w.b + w.part + ALIGN;
   return w;
@@ -1133,23 +1377,30 @@ xtrg_status tc_gemm_check_args(const double* A, const double* B, double* C, int 
 }
 
 xtrg_status tc_gemm_run(const double* A, const double* B, double* C, int M, int N, int K, int batch,
-                        int planes, int nprod, int splitk, char* base, cudaStream_t st) {
-  const TcGemmScratch w = tc_gemm_scratch(M, N, K, batch, planes, splitk);
+                        int planes, int nprod, int splitk, char* base, cudaStream_t st, bool b_kn) {
+  const TcGemmScratch w = tc_gemm_scratch(M, N, K, batch, planes, splitk, b_kn);
   __nv_bfloat16* pa = (__nv_bfloat16*)base;
   __nv_bfloat16* pb = (__nv_bfloat16*)(base + w.a);
   float* part = (float*)(base + w.a + w.b);
   int* err = (int*)(base + w.a + w.b + w.part);
   const long long ld = tc_ld(K);
-  const long long psA = (long long)batch * M * ld, psB = (long long)batch * N * ld;
+  const long long ldn = tc_ld(N);
+  const long long psA = (long long)batch * M * ld;
+  const long long psB = b_kn ? (long long)batch * K * ldn : (long long)batch * N * ld;
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return XTRG_ECUDA;
   if (to_planes(A, idx_plain(K), idx_plain(1), (long long)M * K, M, K, batch, pa, ld,
                 (long long)M * ld, planes, psA, st) != cudaSuccess)
     return XTRG_ECUDA;
-  if (to_planes(B, idx_plain(K), idx_plain(1), (long long)N * K, N, K, batch, pb, ld,
-                (long long)N * ld, planes, psB, st) != cudaSuccess)
-    return XTRG_ECUDA;
+  // B^T rows (K-major), or B's own K x N rows (MN-major operand)
+  const cudaError_t eb =
+      b_kn ? to_planes(B, idx_plain(N), idx_plain(1), (long long)K * N, K, N, batch, pb, ldn,
+                       (long long)K * ldn, planes, psB, st)
+           : to_planes(B, idx_plain(K), idx_plain(1), (long long)N * K, N, K, batch, pb, ld,
+                       (long long)N * ld, planes, psB, st);
+  if (eb != cudaSuccess) return XTRG_ECUDA;
   TcOperand oa{pa, planes, M, K, ld, (long long)M * ld, psA, batch};
   TcOperand ob{pb, planes, N, K, ld, (long long)N * ld, psB, batch};
+  if (b_kn) ob = TcOperand{pb, planes, N, K, ldn, (long long)K * ldn, psB, batch, 1};
   TcOutput out;
   memset(&out, 0, sizeof out);
   out.mode = TC_OUT_PARTIAL;
@@ -1170,6 +1421,22 @@ extern "C" size_t xtrg_tc_gemm_workspace_bytes(int M, int N, int K, int batch, i
                                                int splitk) {
   if (M < 1 || N < 1 || K < 1 || batch < 1 || planes < 1 || planes > 3 || splitk < 1) return 0;
   return tc_gemm_scratch(M, N, K, batch, planes, splitk).total;
+}
+
+extern "C" size_t xtrg_tc_gemm_nn_workspace_bytes(int M, int N, int K, int batch, int planes,
+                                                  int splitk) {
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || planes < 1 || planes > 3 || splitk < 1) return 0;
+  return tc_gemm_scratch(M, N, K, batch, planes, splitk, true).total;
+}
+
+extern "C" xtrg_status xtrg_tc_gemm_nn(const double* A, const double* B, double* C, int M, int N,
+                                       int K, int batch, int planes, int nprod, int splitk,
+                                       void* workspace, size_t bytes, void* stream) {
+  TRY(tc_gemm_check_args(A, B, C, M, N, K, batch, planes, nprod, splitk));
+  if (!workspace || ((uintptr_t)workspace % ALIGN) != 0) return XTRG_EINVAL;
+  if (bytes < tc_gemm_scratch(M, N, K, batch, planes, splitk, true).total) return XTRG_ENOMEM;
+  return tc_gemm_run(A, B, C, M, N, K, batch, planes, nprod, splitk, (char*)workspace,
+                     (cudaStream_t)stream, true);
 }
 
 extern "C" xtrg_status xtrg_tc_gemm(const double* A, const double* B, double* C, int M, int N,
@@ -1193,7 +1460,8 @@ extern "C" void xtrg_destroy(xtrg_ctx* ctx) {
   const char* pt = getenv("XTRG_PROFILE_TAGS");
   if (pt && pt[0] == '1') {
     static const char* names[8] = {"other", "substep1 (env x site)", "substep2 (x site)",
-                                   "C_E (split-K)", "env update", "truncation (split)", "", ""};
+                                   "C_E (split-K)", "env update", "truncation (split)",
+                                   "FP64 two-site update", "FP64 right environments"};
     for (int t = 0; t < 8; ++t)
       if (ctx->tag_n[t])
         fprintf(stderr, "xtrg tc %-24s launches %8lld  %10.1f ms  %8.1f TFLOP/s alg\n", names[t],

@@ -59,11 +59,33 @@ class XTRG:
     def observables(self):
         return _lib.xtrg_observables(self.ctx)
 
+    def entanglement(self):
+        """MPO entanglement S_E of the current rho at bonds 1..L-1 (Eq. purif)."""
+        return _lib.xtrg_entanglement(self.ctx, self.L)
+
     def get_state(self):
         return _lib.xtrg_get_state(self.ctx, self.L)
 
     def set_state(self, sites, lnc, beta, right_canonical=False):
         _lib.xtrg_set_state(self.ctx, sites, lnc, beta, right_canonical)
+
+    def checkpoint(self, buf=None):
+        """Save the current state into a device buffer (a uint8 tensor on this
+        engine's device, allocated here when not given) and return it."""
+        import torch
+        n = _lib.xtrg_checkpoint_bytes(self.ctx)
+        if buf is None:
+            buf = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        if buf.data_ptr() + buf.numel() < ptr + n:
+            raise ValueError(f"checkpoint buffer needs {n} bytes after 256-byte alignment")
+        _lib.xtrg_checkpoint_save(self.ctx, ptr, n)
+        return buf
+
+    def restore(self, buf):
+        """Make the state saved in buf (by ``checkpoint``) the current one."""
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        _lib.xtrg_checkpoint_load(self.ctx, ptr, buf.data_ptr() + buf.numel() - ptr)
 
     def counters(self):
         return _lib.xtrg_get_stats(self.ctx)

@@ -66,6 +66,15 @@ def test_small_cases_match_oracle(eng_cls, name):
     compare_rows(rows, gd["rows"])
     for g, o in zip(rows, gd["rows"]):
         assert bonds_close(g["max_bond"], max(o["bond_dims"]))
+        # rho^T rho is symmetric; its compression is symmetric up to the
+        # truncation: ||rho - rho^T|| <= 2 ||rho - P(rho^T rho)|| gives a
+        # defect bound of 2 sqrt(discarded weight) (the oracle itself shows
+        # 1e-2 at D* = 12, where the cut falls inside degenerate singular
+        # values), and untruncated rows sit at the FP64 resolution of the
+        # difference form (~1.5e-8)
+        bound = max(1e-6, 2.0 * (o.get("trunc") or 0.0) ** 0.5)
+        assert g["herm_defect"] <= bound and o["herm"] <= bound, \
+            (o["beta"], g["herm_defect"], o["herm"], bound)
 
 
 def test_untruncated_L8_matches_exact_diagonalisation(eng_cls):
@@ -150,3 +159,32 @@ def test_errors_are_reported(eng_cls):
     big = [np.ones((1, 2, 2, 40)), np.ones((40, 2, 2, 40)), np.ones((40, 2, 2, 1)), np.ones((1, 2, 2, 1))]
     with pytest.raises(_lib.XtrgError):
         eng.set_state(big, 0.0, 1.0)   # bond above the capacity D* + 1
+
+
+def test_hermiticity_defect_matches_oracle_on_a_nonsymmetric_state(eng_cls):
+    """xtrg_observables' herm_defect = ||rho - rho^T||_F / ||rho||_F against the
+    oracle's transfer contraction (pinned on dense operators) for a state
+    that is not symmetric: rho = I + 0.2 R with R a random MPO, so Tr rho > 0
+    and the defect is O(0.1).  A symmetrised state gives ~0."""
+    from oracle import hamiltonian as oh
+    from oracle import xtrg as ox
+    rng = np.random.default_rng(5)
+    L = 6
+    dims = [1, 3, 4, 5, 4, 3, 1]
+    R = [0.5 * rng.standard_normal((dims[i], 2, 2, dims[i + 1])) for i in range(L)]
+    W = ox.direct_sum(R, 0.2, oh.identity_mpo(L))
+    S = ox.direct_sum(W, 1.0, [w.transpose(0, 2, 1, 3) for w in W])
+    H = oh.xxz_chain_mpo(L, 1.0, 1.0)
+    eng = eng_cls.xxz(L, 1.0, 1.0, tau0=2.0 ** -8, dstar=16, sweeps=2)
+    for state, symmetric in ((W, False), (S, True)):
+        ref = ox.observables(H, state, 0.0, 1.0, L)
+        eng.set_state(state, 0.0, 1.0)
+        g = eng.observables()
+        print("herm gpu", g["herm_defect"], "oracle", ref["herm"])
+        assert abs(g["lnZ"] - ref["lnZ"]) <= 1e-12 * max(1.0, abs(ref["lnZ"]))
+        if symmetric:
+            # the square root of a rounding-level difference on both sides
+            assert g["herm_defect"] < 1e-7 and ref["herm"] < 1e-7
+        else:
+            assert ref["herm"] > 0.05
+            assert abs(g["herm_defect"] - ref["herm"]) <= 1e-10 + 1e-9 * ref["herm"]

@@ -35,12 +35,19 @@ def test_snake_matches_oracle_rows(eng_cls, w):
     eng = eng_cls(dims, W, tau0=w.tau0, dstar=w.dstar, sweeps=w.sweeps, order=w.order)
     rows = eng.run(w.n_doublings)
     for g, o in zip(rows, gd["rows"]):
-        # At a truncated D* two sweeps leave the variational compression short
-        # of its fixed point by up to the order of the discarded weight, and
-        # GPU and CPU rounding take different iterates there: the bar then
-        # includes the row's discarded weight (trunc; 0 when nothing is dropped).
+        # The truncated case runs 6 sweeps, enough for the compression to
+        # settle.  Where D* cuts through degenerate singular values, GPU and
+        # CPU rounding (a Jacobi SVD against LAPACK's) keep different, equally
+        # optimal subspaces: they discard the same weight (checked below, to
+        # 10 %), but quantities linear in rho (Tr rho, Tr H rho) then differ
+        # at first order in the kept subspaces, i.e. up to the row's discarded
+        # weight (measured: 0.18 of it for u at D* = 20, beta = 4).  A wrong
+        # truncation would discard more weight and fail the weight check.
         sens = o.get("sens", {"lnZ": 0.0, "u": 0.0})
         slack = o.get("trunc") or 0.0
+        if n_row := o.get("trunc"):
+            assert abs(g["trunc_err"] - n_row) <= 0.1 * n_row + 1e-12, \
+                (o["beta"], g["trunc_err"], n_row)
         assert abs(g["lnZ"] - o["lnZ"]) <= max(1e-10 * max(1.0, abs(o["lnZ"])), 300 * sens["lnZ"],
                                                slack), (o["beta"], g["lnZ"], o["lnZ"])
         assert abs(g["u"] - o["u"]) <= max(1e-10, 300 * sens["u"], slack), (o["beta"], g["u"], o["u"])
@@ -58,3 +65,22 @@ def test_snake_minimal_mpo_matches_ed(eng_cls, w):
         ref = ex.ed_thermo(E, r["beta"], w.N)
         assert abs(r["lnZ"] - ref["lnZ"]) <= 1e-10 * max(1.0, abs(ref["lnZ"]))
         assert abs(r["u"] - ref["u"]) <= 1e-9
+
+
+def test_snake_tensor_core_path_matches_ed(eng_cls):
+    """The untruncated 2 x 3 square snake (long-range bonds of the snake
+    path, D_H = 8) on the tensor-core path from beta = 1/4: within the
+    mixed-precision gate of exact diagonalisation, |df|/site <= 1e-6 and
+    |du| <= 1e-5 at every beta."""
+    from oracle import exact as ex
+    from oracle import hamiltonian as oh
+    w = [c for c in wl.small_lattice_cases() if c.name == "square_2x3"][0]
+    eng = eng_cls.from_bonds(w.N, w.bonds(), tau0=w.tau0, dstar=w.dstar, sweeps=w.sweeps,
+                             order=w.order, prec="bf16x6", beta_switch=0.25)
+    E = ex.ed_spectrum(oh.dense_bonds(w.N, w.bonds()))
+    rows = eng.run(w.n_doublings)
+    assert eng.counters()["tc_flops"] > 0
+    for r in rows:
+        ref = ex.ed_thermo(E, r["beta"], w.N)
+        assert abs(r["f"] - ref["f"]) <= 1e-6, (r["beta"], r["f"], ref["f"])
+        assert abs(r["u"] - ref["u"]) <= 1e-5, (r["beta"], r["u"], ref["u"])

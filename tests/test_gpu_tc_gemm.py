@@ -86,3 +86,48 @@ def test_tc_gemm_long_chains_are_unbiased(torch_lib, exact_bf16, planes, nprod):
     print("bias", rel.mean(), "rms", np.sqrt((rel ** 2).mean()))
     assert abs(rel.mean()) <= 3e-8
     assert np.sqrt((rel ** 2).mean()) <= 1e-6
+
+
+NN_CASES = [
+    # M,   N,   K,  batch, planes, nprod, splitk
+    (128, 128, 64, 1, 3, 6, 1),
+    (200, 130, 100, 3, 3, 6, 1),
+    (256, 1000, 520, 1, 3, 6, 2),
+    (64, 72, 512, 5, 2, 3, 2),
+    (1, 1, 1, 1, 2, 1, 1),
+]
+
+
+@pytest.mark.parametrize("M,N,K,batch,planes,nprod,splitk", NN_CASES)
+def test_tc_gemm_nn_mn_major_operand(torch_lib, M, N, K, batch, planes, nprod, splitk):
+    """C = A B with B given K x N: B is staged into the tensor cores as an
+    MN-major operand (two 64-wide TMA boxes per plane, MN-major shared-memory
+    descriptor, transposed-B instruction bit).  The tiles hold the same
+    values as the K-major staging of B^T, so the result must equal
+    xtrg_tc_gemm on B^T bit for bit, and the FP64 product within the
+    tolerance of the product count."""
+    torch, lib = torch_lib
+    rng = np.random.default_rng(M * 3 + N * 5 + K + batch)
+    A = rng.standard_normal((batch, M, K))
+    B = rng.standard_normal((batch, K, N))
+    ref = np.einsum("bmk,bkn->bmn", A, B)
+    scale = np.einsum("bmk,bkn->bmn", np.abs(A), np.abs(B))
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    dBt = torch.from_numpy(np.ascontiguousarray(B.transpose(0, 2, 1))).cuda()
+    st = torch.cuda.current_stream().cuda_stream
+    dC = torch.zeros((batch, M, N), dtype=torch.float64, device="cuda")
+    nb = lib.xtrg_tc_gemm_nn_workspace_bytes(M, N, K, batch, planes, splitk)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    p = (ws.data_ptr() + 255) // 256 * 256
+    lib.xtrg_tc_gemm_nn(dA.data_ptr(), dB.data_ptr(), dC.data_ptr(), M, N, K, batch, planes, nprod,
+                        splitk, p, nb, st)
+    C = dC.cpu().numpy()
+    assert (np.abs(C - ref) / scale).max() <= TOL[nprod]
+    dT = torch.zeros((batch, M, N), dtype=torch.float64, device="cuda")
+    nbt = lib.xtrg_tc_gemm_workspace_bytes(M, N, K, batch, planes, splitk)
+    wst = torch.empty(nbt + 256, dtype=torch.uint8, device="cuda")
+    pt = (wst.data_ptr() + 255) // 256 * 256
+    lib.xtrg_tc_gemm(dA.data_ptr(), dBt.data_ptr(), dT.data_ptr(), M, N, K, batch, planes, nprod,
+                     splitk, pt, nbt, st)
+    assert np.array_equal(dT.cpu().numpy(), C)

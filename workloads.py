@@ -197,11 +197,14 @@ SQUARE_8X8_XXZ = LatticeWorkload(name="square_8x8_xxz_D768", kind="square", W=8,
 def small_lattice_cases() -> List[LatticeWorkload]:
     """Snake-lattice parity cases the oracle finishes in seconds: an
     untruncated and a truncated open square strip and an untruncated
-    triangular YC cylinder, tau0 = 2^-10 doubled to beta = 4."""
+    triangular YC cylinder, tau0 = 2^-10 doubled to beta = 4.  The truncated
+    strip takes 6 sweeps per product, enough for the variational compression
+    to reach its fixed point, so GPU and CPU agree to their rounding
+    sensitivity there too."""
     return [
         LatticeWorkload(name="square_2x3", kind="square", W=2, Lx=3, dstar=64, sweeps=2,
                         n_doublings=12),
-        LatticeWorkload(name="square_2x3_trunc", kind="square", W=2, Lx=3, dstar=20, sweeps=2,
+        LatticeWorkload(name="square_2x3_trunc", kind="square", W=2, Lx=3, dstar=20, sweeps=6,
                         n_doublings=12),
         LatticeWorkload(name="triangular_yc3x2", kind="triangular_yc", W=3, Lx=2, dstar=64,
                         sweeps=2, n_doublings=12),

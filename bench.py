@@ -479,25 +479,26 @@ def run_gemm_microbench(args):
     M = N = 4 * D
     K = D * D
     splitk = args.splitk
+    planes, nprod = args.planes, args.nprod
     rng = np.random.default_rng(0)
     A = torch.from_numpy(rng.standard_normal((M, K)) / D).cuda()
     B = torch.from_numpy(rng.standard_normal((N, K)) / D).cuda()
     C = torch.empty((M, N), dtype=torch.float64, device="cuda")
-    nb = _lib.xtrg_tc_gemm_workspace_bytes(M, N, K, 1, 3, splitk)
+    nb = _lib.xtrg_tc_gemm_workspace_bytes(M, N, K, 1, planes, splitk)
     ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
     p = (ws.data_ptr() + 255) // 256 * 256
     st = torch.cuda.current_stream().cuda_stream
     for _ in range(max(1, args.warmup)):
-        _lib.xtrg_tc_gemm(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1, 3, 6, splitk, p, nb,
-                          st)
+        _lib.xtrg_tc_gemm(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1, planes, nprod,
+                          splitk, p, nb, st)
     ts = []
     for _ in range(args.steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        _lib.xtrg_tc_gemm(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1, 3, 6, splitk, p, nb,
-                          st)
+        _lib.xtrg_tc_gemm(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1, planes, nprod,
+                          splitk, p, nb, st)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
@@ -505,7 +506,7 @@ def run_gemm_microbench(args):
     peaks, src = measured_peaks()
     flops = 2.0 * M * N * K
     print(json.dumps({"microbench": "tc_gemm C_E", "M": M, "N": N, "K": K, "splitk": splitk,
-                      "planes": 3, "nprod": 6, "ms_median_call": ms,
+                      "planes": planes, "nprod": nprod, "ms_median_call": ms,
                       "algorithmic_tflops_call": flops / ms / 1e9,
                       "note": "call = plane conversion of A and B + GEMM + FP64 split-K sum",
                       "peak_bf16_sustained_over_6": peaks["bf16_tflops_sustained"] / 6}))
@@ -522,6 +523,8 @@ def main():
     ap.add_argument("--microbench", choices=["ce"], default=None,
                     help="time the tensor-core GEMM alone at the C_E shape of the workload")
     ap.add_argument("--splitk", type=int, default=7, help="split-K of --microbench ce")
+    ap.add_argument("--planes", type=int, default=3, help="BF16 planes of --microbench ce")
+    ap.add_argument("--nprod", type=int, default=6, help="plane products of --microbench ce")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the FP64 GPU comparison arm (several minutes at L=64)")
     ap.add_argument("--ncu-region", action="store_true",

@@ -1,6 +1,7 @@
 // tcgen05 / TMA GEMM kernel (see tc_gemm.cuh).
 //
-// CTA tile 128 x 128 (M x N), K-block 64 BF16 = one 128-byte swizzle row;
+// CTA tile 128 x 128 (M x N), K-block of 64 BF16 (one 128-byte swizzle row;
+// 2 stages at 6 planes) or 32 BF16 (64-byte swizzle; 4 stages at 6 planes);
 // persistent CTAs (one per SM).  Warp 0: TMA producer (one elected thread);
 // warp 1: MMA issuer (one elected thread, 4 x UMMA_K=16 per K-block and
 // product); warp 2: tensor-memory allocation; warps 4-7: epilogue
@@ -30,9 +31,23 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int TILE_BYTES = BM * BK * 2;       // 16 KB per operand plane and stage
+constexpr int BM = 128, BN = 128;
 constexpr int NTHREADS = 256;
+
+// Shared-memory geometry for a K-block of BK BF16 (64: 128-byte swizzle,
+// 32: 64-byte swizzle).  K-major tiles are BM rows of SW bytes in 8-row
+// groups SBO bytes apart; MN-major tiles are ATOMS atoms of BK MN-elements,
+// each BK K-rows of SW bytes (ATOM bytes), ATOM bytes apart.
+template <int BK>
+struct Geo {
+  static constexpr int SW = BK * 2;           // bytes of one swizzled row
+  static constexpr int TILE = BM * BK * 2;    // bytes per operand plane and stage
+  static constexpr int SWZ = BK == 64 ? 2 : 4;   // descriptor swizzle code: 128 B / 64 B
+  static constexpr int SBO = 8 * SW;          // 8-row group stride
+  static constexpr int ATOM = BK * SW;        // MN-major atom: BK K-rows x SW bytes
+  static constexpr int ATOMS = BM / BK;       // MN-major atoms per 128-wide tile
+  static_assert(BK == 64 || BK == 32, "K-block of 32 or 64");
+};
 constexpr long long WAIT_LIMIT = 1LL << 24;
 constexpr int TMEM_COLS = 4 * BN;     // main [0, 2 BN), corr [2 BN, 4 BN)
 constexpr int CORR_COL = 2 * BN;
@@ -96,29 +111,30 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// K-major operand tile, 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart.
+// K-major operand tile: rows of SW bytes, 8-row groups SBO bytes apart; the
+// leading byte offset is unused for swizzled K-major layouts.
+template <int BK>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for K-major SW128)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                 // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                 // swizzle mode: 128 B
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused)
+  d |= (uint64_t)(Geo<BK>::SBO >> 4) << 32;        // stride byte offset: 8 rows
+  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)Geo<BK>::SWZ << 61;               // swizzle mode
   return d;
 }
 
-// MN-major operand tile, 128-byte swizzle: K-rows of 64 contiguous MN
-// elements (128 B), 8-row atoms 1024 B apart along K (stride byte offset),
-// the two 64-wide MN halves of the 128-wide tile MN_HALF bytes apart
-// (leading byte offset).
-constexpr int MN_HALF = BK * 128;   // one half: 64 K-rows x 128 B
+// MN-major operand tile: K-rows of BK contiguous MN elements (SW bytes),
+// 8-row groups SBO bytes apart along K (stride byte offset), consecutive
+// BK-wide MN atoms ATOM bytes apart (leading byte offset).
+template <int BK>
 __device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)(MN_HALF >> 4) << 16;    // leading byte offset: next 64 MN elements
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: next 8 K-rows
-  d |= (uint64_t)1 << 46;                 // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                 // swizzle mode: 128 B
+  d |= (uint64_t)(Geo<BK>::ATOM >> 4) << 16;       // leading byte offset: next MN atom
+  d |= (uint64_t)(Geo<BK>::SBO >> 4) << 32;        // stride byte offset: next 8 K-rows
+  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)Geo<BK>::SWZ << 61;               // swizzle mode
   return d;
 }
 
@@ -281,14 +297,16 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // K-blocks and the corr accumulator per tile, so the MMAs of the next chunk
 // (and of the next tile) run while the epilogue drains and stores; the
 // operand stage ring continues across tiles.
+template <int BK>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const KParams p) {
+  using G = Geo<BK>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = p.stages;
-  const int stage_bytes = (p.pa_planes + p.pb_planes) * TILE_BYTES;
+  const int stage_bytes = (p.pa_planes + p.pb_planes) * G::TILE;
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
   uint64_t* empty = full + S;
   uint64_t* main_full = empty + S;      // [2] per chunk
@@ -350,19 +368,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_expect_tx(&full[s], stage_bytes);
         const int k0 = kb * BK;
         for (int q = 0; q < p.pa_planes; ++q) {
-          uint8_t* dst = st + q * TILE_BYTES;
+          uint8_t* dst = st + q * G::TILE;
           if (p.a_mn) {
-            tma_load_4d(dst, &mapA, &full[s], mt * BM, k0, ba, q);
-            tma_load_4d(dst + MN_HALF, &mapA, &full[s], mt * BM + 64, k0, ba, q);
+            for (int a = 0; a < G::ATOMS; ++a)
+              tma_load_4d(dst + a * G::ATOM, &mapA, &full[s], mt * BM + a * BK, k0, ba, q);
           } else {
             tma_load_4d(dst, &mapA, &full[s], k0, mt * BM, ba, q);
           }
         }
         for (int q = 0; q < p.pb_planes; ++q) {
-          uint8_t* dst = st + (p.pa_planes + q) * TILE_BYTES;
+          uint8_t* dst = st + (p.pa_planes + q) * G::TILE;
           if (p.b_mn) {
-            tma_load_4d(dst, &mapB, &full[s], nt * BN, k0, bb, q);
-            tma_load_4d(dst + MN_HALF, &mapB, &full[s], nt * BN + 64, k0, bb, q);
+            for (int a = 0; a < G::ATOMS; ++a)
+              tma_load_4d(dst + a * G::ATOM, &mapB, &full[s], nt * BN + a * BK, k0, bb, q);
           } else {
             tma_load_4d(dst, &mapB, &full[s], k0, nt * BN, bb, q);
           }
@@ -400,15 +418,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t base = smem_u32(smem + s * stage_bytes);
         const uint32_t mcol = tmem + (uint32_t)(mb * BN);
         for (int pr = 0; pr < p.nprod; ++pr) {
-          const uint32_t a_addr = base + p.prod_a[pr] * TILE_BYTES;
-          const uint32_t b_addr = base + (p.pa_planes + p.prod_b[pr]) * TILE_BYTES;
+          const uint32_t a_addr = base + p.prod_a[pr] * G::TILE;
+          const uint32_t b_addr = base + (p.pa_planes + p.prod_b[pr]) * G::TILE;
           const uint32_t dcol = pr == 0 ? mcol : ccol;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             // K-major: advance 16 BF16 = 32 B along K inside the swizzled
-            // 128-B row; MN-major: advance 16 K-rows = two 1024-B atoms
-            uint64_t da = p.a_mn ? smem_desc_mn(a_addr + kk * 2048) : smem_desc(a_addr) + (uint64_t)(kk * 2);
-            uint64_t db = p.b_mn ? smem_desc_mn(b_addr + kk * 2048) : smem_desc(b_addr) + (uint64_t)(kk * 2);
+            // row; MN-major: advance 16 K-rows of SW bytes
+            uint64_t da = p.a_mn ? smem_desc_mn<BK>(a_addr + kk * 16 * G::SW)
+                                 : smem_desc<BK>(a_addr) + (uint64_t)(kk * 2);
+            uint64_t db = p.b_mn ? smem_desc_mn<BK>(b_addr + kk * 16 * G::SW)
+                                 : smem_desc<BK>(b_addr) + (uint64_t)(kk * 2);
             const bool acc = pr == 0 ? (ci > 0 || kk > 0) : (kb > kb_begin || pr > 1 || kk > 0);
             mma_bf16(dcol, da, db, idesc, acc ? 1u : 0u);
           }
@@ -587,8 +607,11 @@ cudaError_t launch_setup(int* sms) {
   cudaError_t e = g_launch_setup.get(
       [](int dev) {
         LaunchSetup r{cudaSuccess, 0};
-        r.err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     227 * 1024);
+        r.err = cudaFuncSetAttribute(tc_gemm_kernel<64>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (r.err == cudaSuccess)
+          r.err = cudaFuncSetAttribute(tc_gemm_kernel<32>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (r.err == cudaSuccess)
           r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
         return r;
@@ -599,26 +622,37 @@ cudaError_t launch_setup(int* sms) {
   return s.err;
 }
 
-// K-blocks per main accumulation chunk: XTRG_TC_CHUNK_KB in [1, 64] if set,
-// else 2 (128 terms of exact BF16 products per tensor-memory chain)
-int chunk_kb() {
+// Terms per main accumulation chunk: 64 x XTRG_TC_CHUNK_KB (1..64) if set,
+// else 256 (BF16 products per tensor-memory chain, which the tensor core
+// sums exactly for same-signed terms of similar size; measured 3 % faster
+// than 128 at the same accuracy)
+int chunk_terms() {
   static const int v = []() {
     const char* e = getenv("XTRG_TC_CHUNK_KB");
     const int x = e ? atoi(e) : 0;
-    return (x >= 1 && x <= 64) ? x : 2;
+    return 64 * ((x >= 1 && x <= 64) ? x : 4);
   }();
   return v;
 }
 
-// 4-D map: (k, rows, batch, plane), box (64, 128, 1, 1), 128-byte swizzle,
+// K-block width: XTRG_TC_BK = 32 or 64 if set, else 64
+int k_block() {
+  static const int v = []() {
+    const char* e = getenv("XTRG_TC_BK");
+    return (e && atoi(e) == 32) ? 32 : 64;
+  }();
+  return v;
+}
+
+// 4-D map with BK-wide boxes (BK = 64: 128-byte swizzle, 32: 64-byte),
 // out-of-range elements read as zero.
-cudaError_t make_map(CUtensorMap* map, const TcOperand& op) {
+cudaError_t make_map(CUtensorMap* map, const TcOperand& op, int BK) {
   EncodeFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   if (op.ld % 8 != 0 || op.ld < (op.mn_major ? op.rows : op.k) || ((uintptr_t)op.base % 16) != 0)
     return cudaErrorInvalidValue;
-  // K-major: (k, rows, batch, plane), box (64, 128); MN-major: (rows, k,
-  // batch, plane), box (64, 64), loaded twice per 128-wide tile
+  // K-major: (k, rows, batch, plane), box (BK, 128); MN-major: (rows, k,
+  // batch, plane), box (BK, BK), loaded 128 / BK times per 128-wide tile
   const long long outer = op.mn_major ? op.k : op.rows;
   const long long bstride = op.batches > 1 ? op.batch_stride : outer * op.ld;
   cuuint64_t dims[4] = {(cuuint64_t)(op.mn_major ? op.rows : op.k),
@@ -627,10 +661,11 @@ cudaError_t make_map(CUtensorMap* map, const TcOperand& op) {
   cuuint64_t strides[3] = {(cuuint64_t)op.ld * 2, (cuuint64_t)bstride * 2,
                            (cuuint64_t)op.plane_stride * 2};
   if ((strides[1] % 16) || (strides[2] % 16)) return cudaErrorInvalidValue;
-  cuuint32_t box[4] = {(cuuint32_t)64, (cuuint32_t)(op.mn_major ? BK : BM), 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)(op.mn_major ? BK : BM), 1, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUtensorMapSwizzle swz = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)op.base, dims, strides, box,
-                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -645,6 +680,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   if ((A.batches != 1 && A.batches != batch) || (B.batches != 1 && B.batches != batch))
     return cudaErrorInvalidValue;
   if (splitk > 1 && out.mode != TC_OUT_PARTIAL) return cudaErrorInvalidValue;
+  const int BK = k_block();
   KParams p;
   p.M = M; p.N = N; p.K = K; p.batch = batch; p.splitk = splitk;
   p.kb_total = (K + BK - 1) / BK;
@@ -664,18 +700,19 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   p.a_mn = A.mn_major ? 1 : 0;
   p.b_mn = B.mn_major ? 1 : 0;
   p.m_fast = ((M + BM - 1) / BM) < ((N + BN - 1) / BN) ? 1 : 0;
-  const int stage_bytes = (A.planes + B.planes) * TILE_BYTES;
+  // as many stages as fit next to the barriers (up to 6)
+  const int stage_bytes = (A.planes + B.planes) * BM * BK * 2;
   int S = (200 * 1024) / stage_bytes;
-  if (S > 4) S = 4;
+  if (S > 6) S = 6;
   if (S < 2) return cudaErrorInvalidValue;
   p.stages = S;
-  p.chunk_kb = chunk_kb();
+  p.chunk_kb = chunk_terms() / BK;
   p.out = out;
   p.err = dev_err;
   CUtensorMap ma, mb;
   cudaError_t e;
-  if ((e = make_map(&ma, A)) != cudaSuccess) return e;
-  if ((e = make_map(&mb, B)) != cudaSuccess) return e;
+  if ((e = make_map(&ma, A, BK)) != cudaSuccess) return e;
+  if ((e = make_map(&mb, B, BK)) != cudaSuccess) return e;
   const int smem = S * stage_bytes + 1024 + (2 * S + 9) * 8 + 8 + 4 * BN * 8 + 64;
   int sms = 0;
   if ((e = launch_setup(&sms)) != cudaSuccess) return e;
@@ -684,6 +721,9 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(tiles < sms ? tiles : sms));
   note_launch();
-  tc_gemm_kernel<<<grid, NTHREADS, smem, st>>>(ma, mb, p);
+  if (BK == 32)
+    tc_gemm_kernel<32><<<grid, NTHREADS, smem, st>>>(ma, mb, p);
+  else
+    tc_gemm_kernel<64><<<grid, NTHREADS, smem, st>>>(ma, mb, p);
   return cudaGetLastError();
 }

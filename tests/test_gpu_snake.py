@@ -42,12 +42,14 @@ def test_snake_matches_oracle_rows(eng_cls, w):
         # 10 %), but quantities linear in rho (Tr rho, Tr H rho) then differ
         # at first order in the kept subspaces, i.e. up to the row's discarded
         # weight (measured: 0.18 of it for u at D* = 20, beta = 4).  A wrong
-        # truncation would discard more weight and fail the weight check.
+        # truncation would discard more weight than the oracle and fail the
+        # weight check (the GPU may keep a slightly better subspace: measured
+        # 4.9e-3 against the oracle's 5.5e-3; weights below 1e-9 are
+        # rounding-level on both sides).
         sens = o.get("sens", {"lnZ": 0.0, "u": 0.0})
         slack = o.get("trunc") or 0.0
         if n_row := o.get("trunc"):
-            assert abs(g["trunc_err"] - n_row) <= 0.1 * n_row + 1e-12, \
-                (o["beta"], g["trunc_err"], n_row)
+            assert g["trunc_err"] <= 1.1 * n_row + 1e-9, (o["beta"], g["trunc_err"], n_row)
         assert abs(g["lnZ"] - o["lnZ"]) <= max(1e-10 * max(1.0, abs(o["lnZ"])), 300 * sens["lnZ"],
                                                slack), (o["beta"], g["lnZ"], o["lnZ"])
         assert abs(g["u"] - o["u"]) <= max(1e-10, 300 * sens["u"], slack), (o["beta"], g["u"], o["u"])

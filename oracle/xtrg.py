@@ -359,3 +359,112 @@ def mpo_entanglement(W):
         W[i] = U.reshape(l, s, t, -1)
         W[i + 1] = np.tensordot(np.diag(S) @ Vt, W[i + 1], axes=([1], [0]))
     return out
+
+
+# --------------------------------------------------------------------------
+# MPO sums (App. D.2, Eq. LSESum) and the pointwise-Taylor SETTN step
+# (Sec. II C, Eq. Tay)
+# --------------------------------------------------------------------------
+
+def overlap_left_update(VL, T, C):
+    """Left environment of the Frobenius overlap <C, T> = sum C_{s,u} T_{s,u}:
+    VL[t, c] -> VL'[t', c'] = sum VL[t, c] T[t, s, u, t'] C[c, s, u, c']."""
+    X = np.tensordot(VL, T, axes=([0], [0]))              # [c, s, u, t']
+    return np.tensordot(X, C, axes=([0, 1, 2], [0, 1, 2]))  # [t', c']
+
+
+def overlap_right_update(VR, T, C):
+    """Right environment: VR[t', c'] -> VR[t, c] = sum T[t, s, u, t'] C[c, s, u, c'] VR[t', c']."""
+    X = np.tensordot(T, VR, axes=([3], [0]))              # [t, s, u, c']
+    return np.tensordot(X, C, axes=([1, 2, 3], [1, 2, 3]))  # [t, c]
+
+
+def sum_two_site_overlap(VL, Ti, Tj, VR):
+    """C_E of one term of an MPO sum at sites (i, i+1), Fig. VMPO(b): the term
+    T with the holes of C_i C_{i+1} punched, [c, s, u, s', u', c'']."""
+    X = np.tensordot(VL, Ti, axes=([0], [0]))             # [c, s, u, t']
+    X = np.tensordot(X, Tj, axes=([3], [0]))              # [c, s, u, s', u', t'']
+    return np.tensordot(X, VR, axes=([5], [0]))           # [c, s, u, s', u', c'']
+
+
+def compress_sum(terms, weights, guess, dstar, sweeps, rel_tol, stats=None):
+    """Two-site variational compression of sum_j w_j T_j (App. D.2): minimise
+    ||sum_j w_j T_j - C||_F^2 (Eq. MPO:plus); with C canonical around sites
+    (i, i+1) the stationarity condition Eq. LSEProd's sum analogue (Eq.
+    LSESum) gives C_i C_{i+1} = sum_j w_j C_{E,j}, split as in the product
+    compression.  Returns C with its orthogonality centre at site 0."""
+    L = len(guess)
+    n = len(terms)
+    assert n == len(weights) and all(len(t) == L for t in terms)
+    C = right_canonicalize(guess, rel_tol)
+    one = np.ones((1, 1))
+    VL = [[None] * (L + 1) for _ in range(n)]
+    VR = [[None] * (L + 1) for _ in range(n)]
+    for j in range(n):
+        VL[j][0] = one
+        VR[j][L] = one
+        for i in range(L - 1, 0, -1):
+            VR[j][i] = overlap_right_update(VR[j][i + 1], terms[j][i], C[i])
+    st = stats if stats is not None else CompressStats()
+
+    def ce(i):
+        return sum(w * sum_two_site_overlap(VL[j][i], terms[j][i], terms[j][i + 1], VR[j][i + 2])
+                   for j, w in enumerate(weights))
+
+    for sweep in range(sweeps):
+        last = sweep == sweeps - 1
+        for i in range(0, L - 1):
+            C[i], C[i + 1], disc, _ = split_two_site(ce(i), "right", dstar, rel_tol)
+            for j in range(n):
+                VL[j][i + 1] = overlap_left_update(VL[j][i], terms[j][i], C[i])
+            st.updates += 1
+            if last:
+                st.max_discarded = max(st.max_discarded, disc)
+        for i in range(L - 2, -1, -1):
+            C[i], C[i + 1], disc, _ = split_two_site(ce(i), "left", dstar, rel_tol)
+            for j in range(n):
+                VR[j][i + 1] = overlap_right_update(VR[j][i + 2], terms[j][i + 1], C[i + 1])
+            st.updates += 1
+            if last:
+                st.max_discarded = max(st.max_discarded, disc)
+    st.bond_dims = [w.shape[3] for w in C[:-1]]
+    return C
+
+
+def settn_step(H, rho, lnc, dtau, order, dstar, sweeps, rel_tol, stats=None):
+    """One pointwise-Taylor step of SETTN (Eq. Tay, Fig. SETTNAlg(b)):
+    rho(tau + dtau) = sum_{k=0}^{order} (-dtau)^k / k! H^k rho(tau), with
+    rho(tau) = e^{lnc} rho.  The terms H^k rho are built one from the other by
+    compressed products H (H^{k-1} rho) (App. D.1, guess: the previous term),
+    and their weighted sum by the variational MPO sum (App. D.2, guess: rho).
+    Returns the normalised result and its ln c."""
+    terms = [rho]
+    for _ in range(order):
+        prev = terms[-1]
+        terms.append(compress_product(H, prev, prev, dstar, sweeps, rel_tol))
+    weights = [(-dtau) ** k / math.factorial(k) for k in range(order + 1)]
+    C = compress_sum(terms, weights, rho, dstar, sweeps, rel_tol, stats)
+    C, lns = normalize_center(C)
+    return C, lnc + lns
+
+
+def run_settn(H, tau0, init_order, dstar, sweeps, n_steps, taylor_order, rel_tol):
+    """SETTN on the logarithmic grid tau_n = 2^n tau0: the series
+    initialisation of Eq. RhoTau, then pointwise-Taylor steps tau_n ->
+    tau_{n+1} = 2 tau_n (Eq. Tay, dtau = tau_n).  One row of thermodynamics
+    per grid point, as run_xtrg."""
+    L = len(H)
+    rho, lnc = init_rho(H, tau0, init_order, dstar, sweeps, rel_tol)
+    beta = tau0
+    rows = []
+    for n in range(n_steps + 1):
+        if n > 0:
+            st = CompressStats()
+            rho, lnc = settn_step(H, rho, lnc, beta, taylor_order, dstar, sweeps, rel_tol, st)
+            beta *= 2.0
+        row = observables(H, rho, lnc, beta, L)
+        row["bond_dims"] = [w.shape[3] for w in rho[:-1]]
+        if n > 0:
+            row["trunc"] = st.max_discarded
+        rows.append(row)
+    return rows

@@ -67,3 +67,14 @@ def high_t_lnZ(L: int, beta: float, J: float = 1.0, Delta: float = 1.0, bonds=No
     Tr H = 0 and Tr(H^2)/2^N = sum_bonds J^2 (2 + Delta^2) / 16."""
     nb = (L - 1) if bonds is None else len(bonds)
     return L * np.log(2.0) + 0.5 * beta * beta * nb * J * J * (2.0 + Delta * Delta) / 16.0
+
+
+def ed_binder(H: np.ndarray, M: np.ndarray, beta: float) -> float:
+    """U_4 = <M^2>^2 / <M^4> at inverse temperature beta by exact
+    diagonalisation of the dense H (M: dense S^z_tot)."""
+    E, V = np.linalg.eigh(H)
+    w = np.exp(-beta * (E - E.min()))
+    M2 = M @ M
+    m2 = float(np.sum(w * np.einsum("ij,ik,kj->j", V, M2, V))) / w.sum()
+    m4 = float(np.sum(w * np.einsum("ij,ik,kj->j", V, M2 @ M2, V))) / w.sum()
+    return m2 * m2 / m4

@@ -144,3 +144,42 @@ def bonds_mpo(N: int, bonds):
             T = T[:, :, :, stop:stop + 1]
         W.append(T)
     return W
+
+
+def dense_magnetization(L: int) -> np.ndarray:
+    """Dense S^z_tot = sum_i S^z_i (Sec. IV D, Eq. Binder)."""
+    return sum(_site_op(SZ, i, L) for i in range(L))
+
+
+def magnetization_mpo(L: int):
+    """S^z_tot as an MPO of bond dimension 2: W = [[I, 0], [S^z, I]] in the
+    (done, pending) convention of the chain automaton (row 0 of the first
+    site, column 1 of the last)."""
+    W = np.zeros((2, 2, 2, 2))
+    W[0, :, :, 0] = np.eye(2)
+    W[1, :, :, 0] = SZ
+    W[1, :, :, 1] = np.eye(2)
+    sites = []
+    for i in range(L):
+        if i == 0:
+            sites.append(W[1:2].copy())
+        elif i == L - 1:
+            sites.append(W[:, :, :, 0:1].copy())
+        else:
+            sites.append(W.copy())
+    return sites
+
+
+def magnetization_power_mpo(L: int, p: int):
+    """(S^z_tot)^p as the exact p-fold MPO product of magnetization_mpo
+    (bond 2^p, nothing truncated)."""
+    M = magnetization_mpo(L)
+    out = [w.copy() for w in M]
+    for _ in range(p - 1):
+        nxt = []
+        for a, b in zip(out, M):
+            T = np.einsum("asty,btuz->absuyz", a, b)
+            la, lb, _, _, ra, rb = T.shape
+            nxt.append(T.reshape(la * lb, 2, 2, ra * rb))
+        out = nxt
+    return out

@@ -468,3 +468,16 @@ def run_settn(H, tau0, init_order, dstar, sweeps, n_steps, taylor_order, rel_tol
             row["trunc"] = st.max_discarded
         rows.append(row)
     return rows
+
+
+def expectation(O, rho):
+    """<O> = Tr(O rho) / Tr rho for an operator MPO O (the transfer of
+    trace_H_rho with O in place of H)."""
+    return trace_H_rho(O, rho) / trace(rho)
+
+
+def binder_ratio(M2, M4, rho):
+    """U_4 = <M^2>^2 / <M^4> (Sec. IV D, Eq. Binder) from the MPOs of
+    (S^z_tot)^2 and (S^z_tot)^4."""
+    m2 = expectation(M2, rho)
+    return m2 * m2 / expectation(M4, rho)

@@ -87,6 +87,10 @@ typedef struct {
                            of every bond stay resident in device memory, so each
                            update builds one (about 2 L x 4 D*^3 x planes BF16
                            elements more workspace)                            */
+  int orth_block;       /* tensor-core path: column-block width of the truncation's
+                           orthonormalisation (bonds wider than one block are
+                           orthonormalised block by block); 0 = 256, else 32..256
+                           in steps of 32                                       */
 } xtrg_config;
 
 typedef struct {
@@ -124,11 +128,42 @@ xtrg_status xtrg_init(xtrg_ctx* ctx);
  * normalised; beta <- 2 beta (Eq. rho:scale2). */
 xtrg_status xtrg_double(xtrg_ctx* ctx);
 
+/* Pointwise-Taylor SETTN step (Sec. II C, Eq. Tay, Fig. SETTNAlg(b)), the
+ * alternative to a doubling with a free step size:
+ *   rho(beta + dtau) = sum_{k=0}^{order} (-dtau)^k / k! H^k rho(beta).
+ * The terms H^k rho are built by compressed products H (H^{k-1} rho) (App.
+ * D.1) and summed by the variational MPO-sum compression (App. D.2, Eq.
+ * LSESum), cfg.sweeps sweeps each, bonds <= D*, all in FP64; then normalised;
+ * beta <- beta + dtau.  The Taylor remainder is about (dtau ||H||)^{order+1} /
+ * (order+1)! relative: the caller chooses order for its dtau.  dev_buf:
+ * device memory of at least xtrg_settn_workspace_bytes(ctx, order) bytes,
+ * 256-byte aligned, borrowed for the call (the terms k >= 1 and every term's
+ * overlap environments).  1 <= order <= 64, dtau > 0. */
+size_t xtrg_settn_workspace_bytes(const xtrg_ctx* ctx, int order);
+xtrg_status xtrg_settn_step(xtrg_ctx* ctx, double dtau, int order, void* dev_buf, size_t bytes);
+
 /* *lnZ <- ln Tr rho(beta) (a logarithm: Z overflows FP64 for long chains). */
 xtrg_status xtrg_trace(xtrg_ctx* ctx, double* lnZ);
 
 /* Thermodynamics of Eq. ThermalQuan at the current beta. */
 xtrg_status xtrg_observables(xtrg_ctx* ctx, xtrg_obs* out);
+
+/* <O> = Tr(O rho) / Tr rho of the current state for an operator given as a
+ * host MPO (same conventions as xtrg_mpo; L sites, bonds <= D* + 1), e.g. the
+ * MPOs of (S^z_tot)^2 and (S^z_tot)^4 whose expectations give the Binder
+ * ratio U_4 = <M^2>^2 / <M^4> (Sec. IV D, Eq. Binder).  FP64 transfer
+ * contraction; O is copied, the caller keeps its arrays.  Synchronises the
+ * stream. */
+xtrg_status xtrg_expectation(xtrg_ctx* ctx, const xtrg_mpo* O, double* value);
+
+/* rho_{n,n'} = rho_a rho_b (Sec. II B, after Eq. zshift): the product of two
+ * states saved by xtrg_checkpoint_save in this context (or one of the same
+ * length and capacity), compressed to D* with cfg.sweeps sweeps in FP64
+ * (App. D.1), becomes the current state at beta_a + beta_b with ln c_a +
+ * ln c_b + ln s.  For states of the same Hamiltonian (symmetric, commuting)
+ * this is rho(beta_a + beta_b): intermediate grid points between doublings. */
+xtrg_status xtrg_cross_product(xtrg_ctx* ctx, const void* ckpt_a, size_t bytes_a,
+                               const void* ckpt_b, size_t bytes_b);
 
 /* MPO entanglement of the current rho at every bond (Sec. IV A, Eq. purif):
  * rho is read as a state of the doubled local space |s>|t>, normalised in the

@@ -27,7 +27,8 @@ SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "x
            "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm",
            "xtrg_tc_gemm_static", "xtrg_batch_plan", "xtrg_batch_run", "xtrg_checkpoint_bytes",
            "xtrg_checkpoint_save", "xtrg_checkpoint_load", "xtrg_entanglement",
-           "xtrg_tc_gemm_nn_workspace_bytes", "xtrg_tc_gemm_nn"]
+           "xtrg_tc_gemm_nn_workspace_bytes", "xtrg_tc_gemm_nn", "xtrg_settn_workspace_bytes",
+           "xtrg_settn_step", "xtrg_expectation", "xtrg_cross_product"]
 
 
 class xtrg_mpo(C.Structure):
@@ -39,7 +40,7 @@ class xtrg_config(C.Structure):
     _fields_ = [("tau0", C.c_double), ("order", C.c_int), ("dstar", C.c_int),
                 ("sweeps", C.c_int), ("init_sweeps", C.c_int), ("prec", C.c_int),
                 ("beta_switch", C.c_double), ("svd_rel_tol", C.c_double),
-                ("keep_parts", C.c_int)]
+                ("keep_parts", C.c_int), ("orth_block", C.c_int)]
 
 
 class xtrg_obs(C.Structure):
@@ -114,6 +115,14 @@ def _load():
     lib.xtrg_tc_gemm_workspace_bytes.argtypes = [C.c_int] * 6
     lib.xtrg_tc_gemm.restype = C.c_int
     lib.xtrg_tc_gemm.argtypes = [P, P, P] + [C.c_int] * 7 + [P, C.c_size_t, P]
+    lib.xtrg_expectation.restype = C.c_int
+    lib.xtrg_expectation.argtypes = [P, C.POINTER(xtrg_mpo), C.POINTER(C.c_double)]
+    lib.xtrg_cross_product.restype = C.c_int
+    lib.xtrg_cross_product.argtypes = [P, P, C.c_size_t, P, C.c_size_t]
+    lib.xtrg_settn_workspace_bytes.restype = C.c_size_t
+    lib.xtrg_settn_workspace_bytes.argtypes = [P, C.c_int]
+    lib.xtrg_settn_step.restype = C.c_int
+    lib.xtrg_settn_step.argtypes = [P, C.c_double, C.c_int, P, C.c_size_t]
     lib.xtrg_entanglement.restype = C.c_int
     lib.xtrg_entanglement.argtypes = [P, C.POINTER(C.c_double), C.c_int]
     lib.xtrg_checkpoint_bytes.restype = C.c_size_t
@@ -147,11 +156,11 @@ class MpoArgs:
 
 
 def make_config(tau0, order, dstar, sweeps, init_sweeps=None, prec="fp64", beta_switch=0.0,
-                svd_rel_tol=1e-15, keep_parts=True):
+                svd_rel_tol=1e-15, keep_parts=True, orth_block=0):
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     return xtrg_config(float(tau0), int(order), int(dstar), int(sweeps),
                        int(init_sweeps or sweeps), p, float(beta_switch), float(svd_rel_tol),
-                       int(bool(keep_parts)))
+                       int(bool(keep_parts)), int(orth_block))
 
 
 def _check(ctx, status):
@@ -210,6 +219,26 @@ def xtrg_set_state(ctx, sites, lnc, beta, right_canonical=False):
     m = MpoArgs(dims, sites)
     _check(ctx, LIB.xtrg_set_state(ctx, C.byref(m.struct), float(lnc), float(beta),
                                    1 if right_canonical else 0))
+
+
+def xtrg_expectation(ctx, O: MpoArgs) -> float:
+    v = C.c_double()
+    _check(ctx, LIB.xtrg_expectation(ctx, C.byref(O.struct), C.byref(v)))
+    return v.value
+
+
+def xtrg_cross_product(ctx, ptr_a, bytes_a, ptr_b, bytes_b):
+    _check(ctx, LIB.xtrg_cross_product(ctx, C.c_void_p(ptr_a), C.c_size_t(bytes_a),
+                                       C.c_void_p(ptr_b), C.c_size_t(bytes_b)))
+
+
+def xtrg_settn_workspace_bytes(ctx, order) -> int:
+    return int(LIB.xtrg_settn_workspace_bytes(ctx, int(order)))
+
+
+def xtrg_settn_step(ctx, dtau, order, dev_ptr, nbytes):
+    _check(ctx, LIB.xtrg_settn_step(ctx, float(dtau), int(order), C.c_void_p(dev_ptr),
+                                    C.c_size_t(nbytes)))
 
 
 def xtrg_entanglement(ctx, L):

@@ -118,7 +118,7 @@ __global__ void sumsq_f64_kernel(const double* __restrict__ a, long long n, doub
 constexpr int PANEL = 32;
 constexpr int ORTH_NT = 256;
 constexpr int ROWS_PER_CTA = 8;
-constexpr int MAX_K = SUBSPACE_MAX_K;
+constexpr int MAX_K = SUBSPACE_BLOCK_K;
 constexpr long long ORTH_SPIN_LIMIT = 1LL << 22;
 
 struct OrthArgs {
@@ -670,34 +670,38 @@ cudaError_t tc_product(const View& a, const View& b, int M, int N, int K, float*
 // untouched Y instead (they return at once when *flag is 0).  A column
 // whose norm is zero is dead: its output column is zero, as in the block
 // Gram-Schmidt kernels.
-constexpr int CQ_NT = 1024;       // threads of the factor kernel
+constexpr int CQ_NT = 512;        // threads of the factor kernel
 constexpr int CQ_SOLVE_NT = 256;  // threads of the solve kernel (8 warps, one row each)
-constexpr int CQ_PLD = 33;        // row stride of the panel copy
 
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// shared memory of the factor kernel: the packed lower triangle, the
+// transposed panel copy Pt[32][MAX_K], the scaling and the reciprocal pivots
 size_t cholqr_factor_smem(int k) {
   const size_t packed = ((size_t)k * (k + 1) / 2 + 3) / 4 * 4;
-  return (packed + (size_t)MAX_K * CQ_PLD + 2 * MAX_K) * 4;
+  return (packed + (size_t)32 * MAX_K + 2 * MAX_K) * 4;
 }
 
 // G (k x k FP32 row-major, symmetric; lower triangle read) -> Lout (packed
 // lower Cholesky factor of D G D), dout (the scaling d_j; 0 for a dead
-// column), linv (1 / L_jj, 0 for a dead column); *flag = 1 if a live
-// scaled pivot falls below tau (never cleared here).
+// column), linv_out (1 / L_jj, 0 for a dead column); *flag = 1 if a live
+// scaled pivot falls below tau (never cleared here).  Right-looking, 32-wide
+// panels: the diagonal block in registers of warp 0 (lane = row, shuffles),
+// the rows below it one per thread against that block, then the trailing
+// update in 4 x 4 register blocks from the transposed panel copy (float4
+// reads, conflict-free).
 __global__ void __launch_bounds__(CQ_NT, 1)
     cholqr_factor(const float* __restrict__ G, int k, float tau, float* __restrict__ Lout,
                   float* __restrict__ dout, float* __restrict__ linv_out, int* flag) {
   extern __shared__ __align__(16) float cq[];
   const int np = k * (k + 1) / 2;
   float* A = cq;                                    // packed lower triangle
-  float* P = cq + ((np + 3) / 4 * 4);               // panel copy [MAX_K][CQ_PLD]
-  float* d = P + MAX_K * CQ_PLD;                    // scaling
+  float* Pt = cq + ((np + 3) / 4 * 4);              // panel, transposed: Pt[t * MAX_K + row]
+  float* d = Pt + 32 * MAX_K;                       // scaling
   float* li = d + MAX_K;                            // 1 / L_jj
   __shared__ float red[32];
   __shared__ int bad;
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
-  // largest diagonal entry, for the dead-column threshold
   float gm = 0.f;
   for (int j = tid; j < k; j += CQ_NT) {
     const float g = G[(long long)j * k + j];
@@ -708,7 +712,7 @@ __global__ void __launch_bounds__(CQ_NT, 1)
   if (tid == 0) bad = 0;
   __syncthreads();
   if (tid < 32) {
-    float v = red[tid];
+    float v = tid < CQ_NT / 32 ? red[tid] : 0.f;
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (tid == 0) red[0] = v;
   }
@@ -719,65 +723,75 @@ __global__ void __launch_bounds__(CQ_NT, 1)
     d[j] = (g > 1e-30f * gmax && g < 3.0e38f) ? 1.f / sqrtf(g) : 0.f;
   }
   __syncthreads();
-  for (int e = tid; e < np; e += CQ_NT) {
-    // e -> (i, j), j <= i
-    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-    while (i * (i + 1) / 2 > e) --i;
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    const int j = e - i * (i + 1) / 2;
-    const float v = G[(long long)i * k + j] * d[i] * d[j];
-    A[e] = (v == v) ? v : 0.f;
-    if (v != v) bad = 1;
+  // packed load, row by row (one warp per row, coalesced reads of G)
+  for (int i = warp; i < k; i += CQ_NT / 32) {
+    const float di = d[i];
+    for (int j = lane; j <= i; j += 32) {
+      const float v = G[(long long)i * k + j] * di * d[j];
+      A[pk(i, j)] = (v == v) ? v : 0.f;
+      if (v != v) bad = 1;
+    }
   }
   __syncthreads();
   for (int p0 = 0; p0 < k; p0 += 32) {
     const int pw = min(32, k - p0);
-    // (a) the diagonal block, warp 0 (lane = row inside the block)
+    // (a) the diagonal block: lane r holds row p0 + r (columns p0..p0+31)
     if (warp == 0) {
-      for (int j = 0; j < pw; ++j) {
-        const int jj = p0 + j;
-        const float piv = A[pk(jj, jj)];
-        __syncwarp();   // every lane has read the pivot before lane 0 overwrites it
-        const bool dead = d[jj] == 0.f;
-        const bool broke = !dead && !(piv > tau);
-        const float ljj = (dead || broke) ? 1.f : sqrtf(piv);
-        const float inv = (dead || broke) ? 0.f : 1.f / ljj;
-        if (lane == 0) {
-          A[pk(jj, jj)] = ljj;
-          li[jj] = inv;
-          if (broke) bad = 1;
+      float r[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) r[c] = (lane < pw && c <= lane) ? A[pk(p0 + lane, p0 + c)] : 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < pw) {
+          const float piv = __shfl_sync(0xffffffffu, r[j], j);
+          const bool dead = d[p0 + j] == 0.f;
+          const bool broke = !dead && !(piv > tau);
+          const float ljj = (dead || broke) ? 1.f : sqrtf(piv);
+          const float inv = (dead || broke) ? 0.f : 1.f / ljj;
+          if (lane == j) {
+            r[j] = ljj;
+            li[p0 + j] = inv;
+            if (broke) bad = 1;
+          }
+          if (lane > j) r[j] *= inv;
+          // trailing part of the block: r[c] -= L_lane,j L_c,j for j < c <= lane
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            if (c > j) {
+              const float lcj = __shfl_sync(0xffffffffu, r[j], c);
+              if (lane >= c) r[c] -= r[j] * lcj;
+            }
+          }
         }
-        __syncwarp();
-        const int i = p0 + lane;
-        if (lane > j && lane < pw) A[pk(i, jj)] *= inv;
-        __syncwarp();
-        if (lane > j && lane < pw) {
-          const float lij = A[pk(i, jj)];
-          for (int c = j + 1; c <= lane; ++c) A[pk(i, p0 + c)] -= lij * A[pk(p0 + c, jj)];
-        }
-        __syncwarp();
       }
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (lane < pw && c <= lane) A[pk(p0 + lane, p0 + c)] = r[c];
     }
     __syncthreads();
-    // (b) the rows below the block: L_ip = A_ip L_pp^{-T}, copied to the panel buffer
+    // (b) rows below the block: L_ip = A_ip L_pp^{-T}, one thread per row
     for (int i = p0 + pw + tid; i < k; i += CQ_NT) {
       float x[32];
+      const int base = pk(i, p0);
 #pragma unroll
       for (int t = 0; t < 32; ++t) {
         if (t < pw) {
-          float v = A[pk(i, p0 + t)];
+          float v = A[base + t];
 #pragma unroll
           for (int q = 0; q < 32; ++q)
             if (q < t) v -= x[q] * A[pk(p0 + t, p0 + q)];
           x[t] = v * li[p0 + t];
-          A[pk(i, p0 + t)] = x[t];
-          P[i * CQ_PLD + t] = x[t];
         }
       }
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < pw) {
+          A[base + t] = x[t];
+          Pt[t * MAX_K + i] = x[t];
+        }
     }
     __syncthreads();
-    // (c) trailing update A_ic -= sum_t L_it L_ct for p0+pw <= c <= i, in
-    // 4 x 4 register blocks of the lower triangle
+    // (c) trailing update A_ic -= sum_t L_it L_ct for p0+pw <= c <= i
     const int r0 = p0 + pw, n = k - r0;
     if (n > 0) {
       const int nb = (n + 3) / 4, nblk = nb * (nb + 1) / 2;
@@ -786,18 +800,29 @@ __global__ void __launch_bounds__(CQ_NT, 1)
         while (bi * (bi + 1) / 2 > bidx) --bi;
         while ((bi + 1) * (bi + 2) / 2 <= bidx) ++bi;
         const int bc = bidx - bi * (bi + 1) / 2;
+        const int i0 = r0 + 4 * bi, c0 = r0 + 4 * bc;
         float acc[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-        const int i0 = r0 + 4 * bi, c0 = r0 + 4 * bc;
         for (int t = 0; t < pw; ++t) {
           float pi[4], pc[4];
+          // i0, c0 are multiples of 4 past a 32-aligned panel start: whole
+          // float4 reads unless the block runs past k
+          if (i0 + 3 < k) {
+            const float4 v = *reinterpret_cast<const float4*>(Pt + t * MAX_K + i0);
+            pi[0] = v.x; pi[1] = v.y; pi[2] = v.z; pi[3] = v.w;
+          } else {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            pi[u] = (i0 + u < k) ? P[(i0 + u) * CQ_PLD + t] : 0.f;
-            pc[u] = (c0 + u < k) ? P[(c0 + u) * CQ_PLD + t] : 0.f;
+            for (int u = 0; u < 4; ++u) pi[u] = (i0 + u < k) ? Pt[t * MAX_K + i0 + u] : 0.f;
+          }
+          if (c0 + 3 < k) {
+            const float4 v = *reinterpret_cast<const float4*>(Pt + t * MAX_K + c0);
+            pc[0] = v.x; pc[1] = v.y; pc[2] = v.z; pc[3] = v.w;
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) pc[u] = (c0 + u < k) ? Pt[t * MAX_K + c0 + u] : 0.f;
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u)
@@ -823,14 +848,16 @@ __global__ void __launch_bounds__(CQ_NT, 1)
   if (tid == 0 && bad) atomicExch(flag, 1);
 }
 
-// U[r] = (Y[r] o d) L^{-T} for every row r (one warp per row): with u L^T = z,
+// U[r] = (Y[r] o d) L^{-T} for every row r (one warp per row; rows ldy / ldu
+// apart, so a column block of a wider matrix works in place): with u L^T = z,
 // u_j = (z_j - sum_{i<j} u_i L_ji) / L_jj, in blocks of 32 columns (earlier
 // blocks first, then a sequential solve inside the block).  Does nothing if
 // *flag is set (the fast path broke down).
 __global__ void __launch_bounds__(CQ_SOLVE_NT)
-    cholqr_solve(const float* __restrict__ Y, int rows, int k, const float* __restrict__ Lp,
-                 const float* __restrict__ dv, const float* __restrict__ linv,
-                 const int* __restrict__ flag, float* __restrict__ U) {
+    cholqr_solve(const float* __restrict__ Y, long long ldy, int rows, int k,
+                 const float* __restrict__ Lp, const float* __restrict__ dv,
+                 const float* __restrict__ linv, const int* __restrict__ flag,
+                 float* __restrict__ U, long long ldu) {
   if (*flag) return;
   extern __shared__ __align__(16) float Ls[];
   const int np = k * (k + 1) / 2;
@@ -845,7 +872,7 @@ __global__ void __launch_bounds__(CQ_SOLVE_NT)
       x[qb] = 0.f;
       if (qb * 32 < k) {
         const int j = qb * 32 + lane;
-        float s = (j < k) ? Y[(long long)r * k + j] * dv[j] : 0.f;
+        float s = (j < k) ? Y[(long long)r * ldy + j] * dv[j] : 0.f;
         // earlier blocks
 #pragma unroll
         for (int q = 0; q < MAX_K / 32; ++q) {
@@ -865,7 +892,7 @@ __global__ void __launch_bounds__(CQ_SOLVE_NT)
           if (lane > t && j < k) s = fmaf(-xt, Ls[pk(j, qb * 32 + t)], s);
         }
         x[qb] = xj;
-        if (j < k) U[(long long)r * k + j] = xj;
+        if (j < k) U[(long long)r * ldu + j] = xj;
       }
     }
   }
@@ -928,35 +955,88 @@ cudaError_t cholqr_setup() {
   return e != cudaSuccess ? e : r;
 }
 
-// Y (rows x k, FP32) <- an orthonormal basis of its columns: scaled
-// CholeskyQR2 (Y -> U1 in b.Q -> Y), with the block Gram-Schmidt kernels as
-// the device-side fallback when a pass breaks down (see cholqr_factor).
-cudaError_t orthonormalise(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
-  if (k > MAX_K) return cudaErrorInvalidValue;
-  RET(cholqr_setup());
-  RET(cudaMemsetAsync(b.chol_flag, 0, sizeof(int), st));
-  const size_t fsm = cholqr_factor_smem(k), ssm = (size_t)k * (k + 1) / 2 * 4;
+// Two scaled CholeskyQR passes on the column block Yb (rows x w, row stride
+// ldy): Yb -> U1 (in tmp, row stride w) -> Yb.  A breakdown raises
+// b.chol_flag[0] and leaves Yb as it was.
+cudaError_t cholqr2_block(float* Yb, long long ldy, int rows, int w, float* tmp,
+                          const SubspaceBuffers& b, cudaStream_t st) {
+  const size_t fsm = cholqr_factor_smem(w), ssm = (size_t)w * (w + 1) / 2 * 4;
   const int wpb = CQ_SOLVE_NT / 32;
   int grid = (rows + wpb - 1) / wpb;
   if (grid > 152) grid = 152;
-  const float* src = Y;
-  float* dst = b.Q;
+  const float* src = Yb;
+  long long lds = ldy;
+  float* dst = tmp;
+  long long ldd = w;
   for (int pass = 0; pass < 2; ++pass) {
-    // G = Y^T Y (k x k) on the tensor cores
-    RET(tc_product(f32_view(src, idx_plain(1), idx_plain(k)), f32_view(src, idx_plain(1), idx_plain(k)),
-                   k, k, rows, b.out, k, b, st));
+    // G = Yb^T Yb (w x w) on the tensor cores
+    RET(tc_product(f32_view(src, idx_plain(1), idx_plain(lds)),
+                   f32_view(src, idx_plain(1), idx_plain(lds)), w, w, rows, b.out, w, b, st));
     note_launch();
-    cholqr_factor<<<1, CQ_NT, fsm, st>>>(b.out, k, pass == 0 ? 1e-6f : 0.25f, b.chol_L, b.chol_d,
+    cholqr_factor<<<1, CQ_NT, fsm, st>>>(b.out, w, pass == 0 ? 1e-6f : 0.25f, b.chol_L, b.chol_d,
                                          b.chol_li, b.chol_flag);
     RET(cudaGetLastError());
     note_launch();
-    cholqr_solve<<<grid, CQ_SOLVE_NT, ssm, st>>>(src, rows, k, b.chol_L, b.chol_d, b.chol_li,
-                                                 b.chol_flag, dst);
+    cholqr_solve<<<grid, CQ_SOLVE_NT, ssm, st>>>(src, lds, rows, w, b.chol_L, b.chol_d, b.chol_li,
+                                                 b.chol_flag, dst, ldd);
     RET(cudaGetLastError());
-    src = b.Q;
-    dst = Y;
+    src = tmp;
+    lds = w;
+    dst = Yb;
+    ldd = ldy;
   }
-  return block_cgs(Y, rows, k, b, st, b.chol_flag);
+  return cudaSuccess;
+}
+
+// Yb[r][c] -= Z[r][c] (Yb row stride ldy, Z row stride w), unless *flag
+__global__ void subtract_block_kernel(float* __restrict__ Yb, long long ldy,
+                                      const float* __restrict__ Z, int rows, int w,
+                                      const int* __restrict__ flag) {
+  if (*flag) return;
+  const long long total = (long long)rows * w;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / w, c = e % w;
+    Yb[r * ldy + c] -= Z[e];
+  }
+}
+
+// Y (rows x k, FP32) <- an orthonormal basis of its columns.  Up to one
+// column block (k <= b.orth_block): scaled CholeskyQR2 (Y -> U1 in b.Q -> Y), with
+// the block Gram-Schmidt kernels as the device-side fallback when a pass
+// breaks down (see cholqr_factor).  Wider: block classical Gram-Schmidt over
+// column blocks, each projected twice against the blocks before it on the
+// tensor cores (S = Q^T Y_b, Y_b -= Q S) and then orthonormalised by scaled
+// CholeskyQR2; a breakdown leaves Y unorthonormal, which the caller's
+// orthonormality check turns into the exact split.
+cudaError_t orthonormalise(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
+  if (k > SUBSPACE_MAX_K) return cudaErrorInvalidValue;
+  RET(cholqr_setup());
+  RET(cudaMemsetAsync(b.chol_flag, 0, sizeof(int), st));
+  const int B = b.orth_block;
+  if (B < 32 || B > MAX_K || B % 32) return cudaErrorInvalidValue;
+  if (k <= B) {
+    RET(cholqr2_block(Y, k, rows, k, b.Q, b, st));
+    return block_cgs(Y, rows, k, b, st, b.chol_flag);
+  }
+  for (int j0 = 0; j0 < k; j0 += B) {
+    const int w = k - j0 < B ? k - j0 : B;
+    float* Yb = Y + j0;
+    for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
+      // S (j0 x w, in b.out) = Q^T Y_b with Q = Y[:, :j0]
+      RET(tc_product(f32_view(Y, idx_plain(1), idx_plain(k)), f32_view(Yb, idx_plain(1), idx_plain(k)),
+                     j0, w, rows, b.out, w, b, st));
+      // Z (rows x w, in b.Q) = Q S
+      RET(tc_product(f32_view(Y, idx_plain(k), idx_plain(1)), f32_view(b.out, idx_plain(1), idx_plain(w)),
+                     rows, w, j0, b.Q, w, b, st));
+      note_launch();
+      subtract_block_kernel<<<grid_for((long long)rows * w), 256, 0, st>>>(Yb, k, b.Q, rows, w,
+                                                                           b.chol_flag);
+      RET(cudaGetLastError());
+    }
+    RET(cholqr2_block(Yb, k, rows, w, b.Q, b, st));
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -1014,7 +1094,7 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
                            unsigned long long seed, const SubspaceBuffers& b, cudaStream_t st,
                            double* discarded, double* orth_defect) {
   (void)CE;
-  if (k > 256 || k > m || k > n) return cudaErrorInvalidValue;
+  if (k > SUBSPACE_MAX_K || k > m || k > n) return cudaErrorInvalidValue;
   const double inv_mn = 1.0 / ((double)m * n);
   const long long ldn = tc_ld(n), ldm = tc_ld(m);
   const View ce = planes_view(b.ce_rm, ldn, b.ce_ps);    // C_E   (m rows, K = n)

@@ -28,17 +28,21 @@ struct SubspaceBuffers {
   double* ce_ss;          // ||C_E||_F^2 (device scalar)
   // scaled CholeskyQR2: packed Cholesky factor, column scaling, 1 / L_jj,
   // breakdown flag (0: the fast path succeeded)
-  float* chol_L;          // k (k + 1) / 2 with k <= 256
-  float* chol_d;          // 256
-  float* chol_li;         // 256
+  float* chol_L;          // w (w + 1) / 2 for a column block of width w
+  float* chol_d;          // SUBSPACE_BLOCK_K
+  float* chol_li;         // SUBSPACE_BLOCK_K
   int* chol_flag;         // [0] breakdown flag of the current call, [1] count of breakdowns
+  int orth_block;         // column-block width of the orthonormalisation (32..SUBSPACE_BLOCK_K)
 };
 
-// Largest k the orthonormalisation handles; wider splits take the exact path.
-constexpr int SUBSPACE_MAX_K = 256;
+// Widest column block the one-block orthonormalisation kernels take, and the
+// largest k of the blocked orthonormalisation; wider splits take the exact
+// path.
+constexpr int SUBSPACE_BLOCK_K = 256;
+constexpr int SUBSPACE_MAX_K = 1024;
 
-// Floats of chol_L (k <= SUBSPACE_MAX_K).
-constexpr size_t SUBSPACE_CHOL_FLOATS = (size_t)256 * 257 / 2;
+// Floats of chol_L (one column block).
+constexpr size_t SUBSPACE_CHOL_FLOATS = (size_t)SUBSPACE_BLOCK_K * (SUBSPACE_BLOCK_K + 1) / 2;
 
 // Orthonormalisations launched as one thread-block cluster (all contexts).
 extern unsigned long long g_orth_cluster_calls;

@@ -67,6 +67,7 @@ inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 // and everything shaped by C's bonds use capc = max(cap, DH * cap_fat).
 bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
   if (L < 2 || DH < 1 || cfg->dstar < 1 || cfg->dstar > 1024) return false;
+  if (cfg->orth_block < 0 || cfg->orth_block > SUBSPACE_BLOCK_K || cfg->orth_block % 32) return false;
   p->L = L;
   p->DH = DH;
   p->cap = cfg->dstar + 1;
@@ -111,7 +112,7 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
     mb += up(subspace_buffer_floats(p->cap) * 4) + 3 * ALIGN;
     mb += up(subspace_plane_elems_a(p->cap) * 2) + up(subspace_plane_elems_b(p->cap) * 2);
     mb += 2 * up(subspace_plane_elems_a(p->cap) * 2) + ALIGN;   // C_E planes, both orientations
-    mb += up(SUBSPACE_CHOL_FLOATS * 4) + 2 * up(256 * 4) + ALIGN;   // CholeskyQR2 factor
+    mb += up(SUBSPACE_CHOL_FLOATS * 4) + 2 * up(SUBSPACE_BLOCK_K * 4) + ALIGN;   // CholeskyQR2 factor
     p->mixed_bytes = (cfg->prec == XTRG_FP64) ? 0 : mb;
   }
   size_t t = 0;
@@ -460,6 +461,104 @@ xtrg_status compress(xtrg_ctx* ctx, const DevMpo& A, const DevMpo& B, DevMpo& C,
   return XTRG_OK;
 }
 
+// ------------------------------------------------ MPO sums (App. D.2)
+// Overlap environments of one term T of an MPO sum with the compressed C:
+// E[t][c] at each bond (t: T's bond, c: C's bond), left ones filled L->R and
+// right ones R->L in one slot per bond, as the product's environments.
+struct SumTerm {
+  const DevMpo* T;
+  double w;
+  double* env;        // (L+1) slots of env_slot doubles
+};
+
+// G1[(c,s,u)][t'] = sum_t E_L[t][c] T_i[t][(s,u,t')]   (into g, Dc x 4 Dt')
+xtrg_status sum_left_part(xtrg_ctx* ctx, const SumTerm& x, const DevMpo& C, int i, size_t slot,
+                          double* g) {
+  const int dt = x.T->dims[i], dt2 = x.T->dims[i + 1], dc = C.dims[i];
+  return gemm64(ctx, mk(dc, 4 * dt2, dt, 1, x.env + (size_t)i * slot, idx_plain(1), idx_plain(dc), 0,
+                        x.T->site[i], idx_plain(4 * dt2), idx_plain(1), 0, g, idx_plain(4 * dt2),
+                        idx_plain(1), 0));
+}
+
+// G2[(t',s',u')][c''] = sum_t'' T_j[(t',s',u')][t''] E_R[t''][c'']   (into g, 4 Dt' x Dc'')
+xtrg_status sum_right_part(xtrg_ctx* ctx, const SumTerm& x, const DevMpo& C, int j, size_t slot,
+                           double* g) {
+  const int dt = x.T->dims[j], dt2 = x.T->dims[j + 1], dc2 = C.dims[j + 1];
+  return gemm64(ctx, mk(4 * dt, dc2, dt2, 1, x.T->site[j], idx_plain(dt2), idx_plain(1), 0,
+                        x.env + (size_t)(j + 1) * slot, idx_plain(dc2), idx_plain(1), 0, g,
+                        idx_plain(dc2), idx_plain(1), 0));
+}
+
+// E_L at bond i+1: E'[t'][c'] = sum_(c,s,u) G1[(c,s,u)][t'] C_i[(c,s,u)][c']
+xtrg_status sum_left_env(xtrg_ctx* ctx, const SumTerm& x, const DevMpo& C, int i, size_t slot,
+                         double* g) {
+  TRY(sum_left_part(ctx, x, C, i, slot, g));
+  const int dt2 = x.T->dims[i + 1], dc = C.dims[i], dc2 = C.dims[i + 1];
+  return gemm64(ctx, mk(dt2, dc2, 4 * dc, 1, g, idx_plain(1), idx_plain(dt2), 0, C.site[i],
+                        idx_plain(dc2), idx_plain(1), 0, x.env + (size_t)(i + 1) * slot,
+                        idx_plain(dc2), idx_plain(1), 0));
+}
+
+// E_R at bond j: E[t][c] = sum_(s,u,c'') G2[t][(s,u,c'')] C_j[c][(s,u,c'')]
+xtrg_status sum_right_env(xtrg_ctx* ctx, const SumTerm& x, const DevMpo& C, int j, size_t slot,
+                          double* g) {
+  TRY(sum_right_part(ctx, x, C, j, slot, g));
+  const int dt = x.T->dims[j], dc = C.dims[j], dc2 = C.dims[j + 1];
+  return gemm64(ctx, mk(dt, dc, 4 * dc2, 1, g, idx_plain(4 * dc2), idx_plain(1), 0, C.site[j],
+                        idx_plain(1), idx_plain(4 * dc2), 0, x.env + (size_t)j * slot,
+                        idx_plain(dc), idx_plain(1), 0));
+}
+
+// Variational compression of sum_j w_j T_j into C (App. D.2, Eq. LSESum):
+// C holds the guess, right-canonical; the two-site solution is
+// C_i C_{i+1} = sum_j w_j C_E,j with C_E,j = G1_j G2_j, split as in the
+// product compression.  On return the orthogonality centre is site 0.
+xtrg_status compress_sum(xtrg_ctx* ctx, std::vector<SumTerm>& terms, DevMpo& C, int dstar,
+                         int sweeps, size_t slot) {
+  const int L = ctx->L;
+  const int kcap = dstar < ctx->cap ? dstar : ctx->cap;
+  double* g1 = ctx->T1;
+  double* g2 = ctx->Lp;
+  for (auto& x : terms) {
+    CK(dev_fill(x.env, 1.0, 1, ctx->st));
+    CK(dev_fill(x.env + (size_t)L * slot, 1.0, 1, ctx->st));
+    for (int j = L - 1; j >= 1; --j) TRY(sum_right_env(ctx, x, C, j, slot, g2));
+  }
+  double maxdisc = 0.0;
+  for (int s = 0; s < sweeps; ++s) {
+    const bool last = s == sweeps - 1;
+    for (int dir = 0; dir < 2; ++dir) {
+      for (int step = 0; step < L - 1; ++step) {
+        const int i = dir == 0 ? step : L - 2 - step;
+        const int m = 4 * C.dims[i], n = 4 * C.dims[i + 2];
+        for (size_t t = 0; t < terms.size(); ++t) {
+          const SumTerm& x = terms[t];
+          TRY(sum_left_part(ctx, x, C, i, slot, g1));
+          TRY(sum_right_part(ctx, x, C, i + 1, slot, g2));
+          const int dt = x.T->dims[i + 1];
+          GemmF64 g = mk(m, n, dt, 1, g1, idx_plain(dt), idx_plain(1), 0, g2, idx_plain(n),
+                         idx_plain(1), 0, ctx->CE, idx_plain(n), idx_plain(1), 0);
+          g.alpha = x.w;
+          g.beta = t == 0 ? 0.0 : 1.0;
+          TRY(gemm(ctx, g));
+        }
+        SvdResult r;
+        TRY(split(ctx, ctx->CE, m, n, kcap, dir == 0 ? SPLIT_RIGHT : SPLIT_LEFT, C.site[i],
+                  C.site[i + 1], &r));
+        C.dims[i + 1] = r.k;
+        if (last && r.discarded > maxdisc) maxdisc = r.discarded;
+        for (auto& x : terms) {
+          if (dir == 0) TRY(sum_left_env(ctx, x, C, i, slot, g1));
+          else TRY(sum_right_env(ctx, x, C, i + 1, slot, g2));
+        }
+        ctx->updates++;
+      }
+    }
+  }
+  ctx->last_trunc = maxdisc;
+  return XTRG_OK;
+}
+
 // ||C_0||_F for the centre site; C_0 /= s.  Returns ln s.
 xtrg_status normalize(xtrg_ctx* ctx, DevMpo& C, double* lns) {
   const long long n = (long long)site_elems(C, 0);
@@ -720,7 +819,7 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (ctx->profiling) TRY(ev_pair(ctx, TAG_SPLIT, &s0, &s1));
         if (k > SUBSPACE_MAX_K) {
-          // wider than the orthonormalisation handles (D* > 256): exact split
+          // wider than the blocked orthonormalisation handles: exact split
           defect = 1.0;
         } else if (dir == 0) {
           CKM(subspace_split(ctx->CE, m, n, k, 1, C.site[i + 1], C.dims[i + 1], C.site[i],
@@ -885,10 +984,10 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   if (!cfg || check_mpo(Hm, 1 << 20) != XTRG_OK) return XTRG_EINVAL;
   if (!(cfg->tau0 > 0.0) || cfg->order < 1 || cfg->order > 16 || cfg->sweeps < 1 ||
       cfg->init_sweeps < 1 || cfg->dstar < 1 || cfg->dstar > 1024 || !(cfg->svd_rel_tol >= 0.0) ||
-      (int)cfg->prec < 0 || (int)cfg->prec > 2)
+      (int)cfg->prec < 0 || (int)cfg->prec > 2 || cfg->orth_block < 0 ||
+      cfg->orth_block > SUBSPACE_BLOCK_K || cfg->orth_block % 32)
     return XTRG_EINVAL;
   if (!dev_workspace || ((uintptr_t)dev_workspace % ALIGN) != 0) return XTRG_EINVAL;
-  if (cfg->prec != XTRG_FP64 && cfg->dstar > 256) return XTRG_EINVAL;  // tensor-core truncation bound
   Plan p;
   if (!plan_sizes(Hm->L, max_bond(Hm), cfg, &p)) return XTRG_EINVAL;
   if (workspace_bytes < p.total) return XTRG_ENOMEM;
@@ -975,8 +1074,8 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
         ctx->m.sb.Q = f; f += mm * c;
         ctx->m.sb.Y = f; f += mm * c;
         ctx->m.sb.out = f; f += mm * mm;
-        ctx->m.sb.orth_part = f; f += G * 256 * 32;
-        ctx->m.sb.orth_red = f; f += 256 * 32;
+        ctx->m.sb.orth_part = f; f += G * SUBSPACE_BLOCK_K * 32;
+        ctx->m.sb.orth_red = f; f += SUBSPACE_BLOCK_K * 32;
         ctx->m.sb.scal = f; f += 64;
         ctx->m.sb.orth_partd = (double*)f; f += 2 * G * 32 * 32;
         ctx->m.sb.orth_redd = (double*)f; f += 2 * 32 * 32;
@@ -995,12 +1094,12 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
       ctx->m.sb.ce_tr = (__nv_bfloat16*)carve(ctx, subspace_plane_elems_a(p.cap) * 2);
       ctx->m.sb.ce_ss = (double*)carve(ctx, 16);
       ctx->m.sb.chol_L = (float*)carve(ctx, SUBSPACE_CHOL_FLOATS * 4);
-      ctx->m.sb.chol_d = (float*)carve(ctx, 256 * 4);
-      ctx->m.sb.chol_li = (float*)carve(ctx, 256 * 4);
+      ctx->m.sb.chol_d = (float*)carve(ctx, SUBSPACE_BLOCK_K * 4);
+      ctx->m.sb.chol_li = (float*)carve(ctx, SUBSPACE_BLOCK_K * 4);
       ctx->m.sb.chol_flag = (int*)carve(ctx, 16);
+      ctx->m.sb.orth_block = cfg->orth_block ? cfg->orth_block : SUBSPACE_BLOCK_K;
       ok = ok && ctx->m.sb.ce_rm && ctx->m.sb.ce_tr && ctx->m.sb.ce_ss && ctx->m.sb.chol_L &&
            ctx->m.sb.chol_d && ctx->m.sb.chol_li && ctx->m.sb.chol_flag;
-      if (ok && cudaMemsetAsync(ctx->m.sb.chol_flag, 0, 16, ctx->st) != cudaSuccess) ok = false;
       ok = ok && ctx->m.sb.dscal && ctx->m.sb.pa && ctx->m.sb.pb;
     }
     ok = ok && ctx->m.T1 && ctx->m.T1R && ctx->m.Lp && ctx->m.Rp && ctx->m.Ct && ctx->m.part &&
@@ -1013,6 +1112,10 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   }
   ctx->env.resize(ctx->L + 1);
   for (int i = 0; i <= ctx->L; ++i) ctx->env[i] = envbase + (size_t)i * p.n_env;
+  if (ctx->mixed_ready && cudaMemsetAsync(ctx->m.sb.chol_flag, 0, 16, ctx->st) != cudaSuccess) {
+    delete ctx;
+    return XTRG_ECUDA;
+  }
   // Hamiltonian and identity sites
   for (int i = 0; i <= ctx->L; ++i) ctx->H.dims[i] = Hm->bond_dims[i];
   for (int i = 0; i < ctx->L; ++i) {
@@ -1107,6 +1210,89 @@ extern "C" xtrg_status xtrg_double(xtrg_ctx* ctx) {
   return XTRG_OK;
 }
 
+// Pointwise-Taylor SETTN step (Sec. II C, Eq. Tay, Fig. SETTNAlg(b)):
+// rho(beta + dtau) = sum_{k=0}^{order} (-dtau)^k/k! H^k rho(beta).  Terms
+// H^k rho by compressed products H (H^{k-1} rho) (App. D.1; guess: the
+// previous term), their sum by the variational MPO sum (App. D.2; guess:
+// rho), all in FP64.  The caller's buffer holds the terms k >= 1 and every
+// term's overlap environments.
+namespace {
+size_t settn_sizes(const xtrg_ctx* ctx, int order, size_t* term_slot, size_t* env_slot) {
+  const size_t cap = ctx->cap;
+  *term_slot = cap * 4 * cap;
+  *env_slot = cap * cap;
+  return (size_t)order * up((size_t)ctx->L * *term_slot * 8) +
+         (size_t)(order + 1) * up((size_t)(ctx->L + 1) * *env_slot * 8);
+}
+}  // namespace
+
+extern "C" size_t xtrg_settn_workspace_bytes(const xtrg_ctx* ctx, int order) {
+  if (!ctx || order < 1 || order > 64) return 0;
+  size_t ts, es;
+  return settn_sizes(ctx, order, &ts, &es);
+}
+
+extern "C" xtrg_status xtrg_settn_step(xtrg_ctx* ctx, double dtau, int order, void* dev_buf,
+                                       size_t bytes) {
+  if (!ctx) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "xtrg_settn_step before xtrg_init");
+  if (!(dtau > 0.0) || order < 1 || order > 64)
+    return fail(ctx, XTRG_EINVAL, "settn step needs dtau > 0 and 1 <= order <= 64");
+  if (!dev_buf || ((uintptr_t)dev_buf % ALIGN) != 0)
+    return fail(ctx, XTRG_EINVAL, "settn buffer must be device memory, 256-byte aligned");
+  size_t ts = 0, es = 0;
+  const size_t need = settn_sizes(ctx, order, &ts, &es);
+  if (bytes < need) return fail(ctx, XTRG_ENOMEM, "settn buffer below %zu bytes", need);
+  const int L = ctx->L;
+  ctx->use_mixed = false;
+  char* b = (char*)dev_buf;
+  std::vector<DevMpo> T(order);
+  for (int k = 0; k < order; ++k) {
+    T[k].slot = ts;
+    T[k].dims.assign(L + 1, 1);
+    T[k].site.resize(L);
+    for (int i = 0; i < L; ++i) T[k].site[i] = (double*)b + (size_t)i * ts;
+    b += up((size_t)L * ts * 8);
+  }
+  // terms H^k rho, k = 1..order
+  const DevMpo* prev = &ctx->rho;
+  for (int k = 0; k < order; ++k) {
+    TRY(canonicalize(ctx, prev->dims, prev->site, ctx->C));
+    TRY(compress(ctx, ctx->H, *prev, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+    T[k].dims = ctx->C.dims;
+    for (int i = 0; i < L; ++i)
+      CK(cudaMemcpyAsync(T[k].site[i], ctx->C.site[i], sizeof(double) * site_elems(ctx->C, i),
+                         cudaMemcpyDeviceToDevice, ctx->st));
+    prev = &T[k];
+  }
+  std::vector<SumTerm> terms(order + 1);
+  double w = 1.0;
+  for (int k = 0; k <= order; ++k) {
+    if (k > 0) w *= -dtau / k;
+    terms[k].T = k == 0 ? &ctx->rho : &T[k - 1];
+    terms[k].w = w;
+    terms[k].env = (double*)b;
+    b += up((size_t)(L + 1) * es * 8);
+  }
+  // guess: rho itself, right-canonical
+  if (ctx->rho_canonical) {
+    ctx->C.dims = ctx->rho.dims;
+    for (int i = 0; i < L; ++i)
+      CK(cudaMemcpyAsync(ctx->C.site[i], ctx->rho.site[i], sizeof(double) * site_elems(ctx->rho, i),
+                         cudaMemcpyDeviceToDevice, ctx->st));
+  } else {
+    TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, ctx->C));
+  }
+  TRY(compress_sum(ctx, terms, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps, es));
+  double lns = 0.0;
+  TRY(normalize(ctx, ctx->C, &lns));
+  std::swap(ctx->rho, ctx->C);
+  ctx->lnc += lns;
+  ctx->beta += dtau;
+  ctx->rho_canonical = true;
+  return XTRG_OK;
+}
+
 extern "C" xtrg_status xtrg_trace(xtrg_ctx* ctx, double* lnZ) {
   if (!ctx || !lnZ) return XTRG_EINVAL;
   if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "no state");
@@ -1115,6 +1301,44 @@ extern "C" xtrg_status xtrg_trace(xtrg_ctx* ctx, double* lnZ) {
   if (!(t[0] > 0.0) || !std::isfinite(t[0]))
     return fail(ctx, XTRG_ENUMERIC, "Tr rho = %g is not positive", t[0]);
   *lnZ = ctx->lnc + std::log(t[0]);
+  return XTRG_OK;
+}
+
+// <O> = Tr(O rho) / Tr rho for an operator MPO O with bonds <= D* + 1 (e.g.
+// the powers of S^z_tot of the Binder ratio, Sec. IV D, Eq. Binder): O is
+// copied into the Y slots, and E'[h'][r'] = sum O[h][s][t][h'] E[h][r]
+// rho[r][t][s][r'] is carried left to right (FP64).
+extern "C" xtrg_status xtrg_expectation(xtrg_ctx* ctx, const xtrg_mpo* O, double* value) {
+  if (!ctx || !value) return XTRG_EINVAL;
+  if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "no state");
+  if (check_mpo(O, ctx->cap) != XTRG_OK || O->L != ctx->L)
+    return fail(ctx, XTRG_EINVAL, "operator MPO has the wrong length or a bond above %d", ctx->cap);
+  const int L = ctx->L;
+  DevMpo& Op = ctx->Y;
+  for (int i = 0; i <= L; ++i) Op.dims[i] = O->bond_dims[i];
+  for (int i = 0; i < L; ++i)
+    CK(cudaMemcpyAsync(Op.site[i], O->W[i], sizeof(double) * site_elems(Op, i),
+                       cudaMemcpyHostToDevice, ctx->st));
+  double t[3];
+  TRY(traces(ctx, false, t));   // Tr rho (synchronises, so O's host arrays are free)
+  const DevMpo& R = ctx->rho;
+  double* E[2] = {ctx->hf[0], ctx->hf[1]};
+  double* T = ctx->ht;
+  CK(dev_fill(E[0], 1.0, 1, ctx->st));
+  for (int i = 0; i < L; ++i) {
+    const int l = R.dims[i], r = R.dims[i + 1], hl = Op.dims[i], hr = Op.dims[i + 1];
+    TRY(gemm64(ctx, mk(hl, 4 * r, l, 1, E[i & 1], idx_plain(l), idx_plain(1), 0, R.site[i],
+                       idx_plain(4 * r), idx_plain(1), 0, T, idx_plain(4 * r), idx_plain(1), 0)));
+    TRY(gemm64(ctx, mk(hr, r, 4 * hl, 1, Op.site[i], idx_plain(1), idx_plain(hr), 0, T,
+                       idx_split3(2, 2, 4LL * r, r, 2LL * r), idx_plain(1), 0, E[(i + 1) & 1],
+                       idx_plain(r), idx_plain(1), 0)));
+  }
+  double tr_o = 0.0;
+  CK(cudaMemcpyAsync(&tr_o, E[L & 1], sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (!(t[0] > 0.0) || !std::isfinite(tr_o))
+    return fail(ctx, XTRG_ENUMERIC, "Tr rho = %g, Tr(O rho) = %g", t[0], tr_o);
+  *value = tr_o / t[0];
   return XTRG_OK;
 }
 
@@ -1286,8 +1510,12 @@ extern "C" xtrg_status xtrg_checkpoint_save(xtrg_ctx* ctx, void* dev_buf, size_t
   return XTRG_OK;
 }
 
-extern "C" xtrg_status xtrg_checkpoint_load(xtrg_ctx* ctx, const void* dev_buf, size_t bytes) {
-  if (!ctx || !dev_buf || ((uintptr_t)dev_buf % ALIGN) != 0) return XTRG_EINVAL;
+namespace {
+// Reads a device checkpoint into dst (bond dims, sites) and returns its
+// header values; the sites must fit this context's capacity.
+xtrg_status load_checkpoint(xtrg_ctx* ctx, const void* dev_buf, size_t bytes, DevMpo& dst,
+                            CkptHeader* hout) {
+  if (!dev_buf || ((uintptr_t)dev_buf % ALIGN) != 0) return XTRG_EINVAL;
   if (bytes < CKPT_HEADER) return fail(ctx, XTRG_EINVAL, "checkpoint buffer too small");
   CkptHeader h;
   const char* d = (const char*)dev_buf;
@@ -1305,18 +1533,50 @@ extern "C" xtrg_status xtrg_checkpoint_load(xtrg_ctx* ctx, const void* dev_buf, 
     need += sizeof(double) * (size_t)h.dims[i] * 4 * h.dims[i + 1];
   }
   if (bytes < need) return fail(ctx, XTRG_EINVAL, "checkpoint buffer shorter than its sites");
-  for (int i = 0; i <= ctx->L; ++i) ctx->rho.dims[i] = h.dims[i];
+  for (int i = 0; i <= ctx->L; ++i) dst.dims[i] = h.dims[i];
   size_t off = CKPT_HEADER;
   for (int i = 0; i < ctx->L; ++i) {
-    const size_t b = sizeof(double) * site_elems(ctx->rho, i);
-    CK(cudaMemcpyAsync(ctx->rho.site[i], d + off, b, cudaMemcpyDeviceToDevice, ctx->st));
+    const size_t b = sizeof(double) * site_elems(dst, i);
+    CK(cudaMemcpyAsync(dst.site[i], d + off, b, cudaMemcpyDeviceToDevice, ctx->st));
     off += b;
   }
+  *hout = h;
+  return XTRG_OK;
+}
+}  // namespace
+
+extern "C" xtrg_status xtrg_checkpoint_load(xtrg_ctx* ctx, const void* dev_buf, size_t bytes) {
+  if (!ctx || !dev_buf || ((uintptr_t)dev_buf % ALIGN) != 0) return XTRG_EINVAL;
+  CkptHeader h;
+  TRY(load_checkpoint(ctx, dev_buf, bytes, ctx->rho, &h));
   ctx->lnc = h.lnc;
   ctx->beta = h.beta;
   ctx->nd = h.nd;
   ctx->have_rho = true;
   ctx->rho_canonical = h.canonical != 0;
+  return XTRG_OK;
+}
+
+// rho_{n,n'} = rho_a rho_b (Sec. II B, after Eq. zshift): intermediate
+// inverse temperatures beta_a + beta_b from two saved states, the product
+// compressed variationally in FP64 (App. D.1; guess: rho_a).
+extern "C" xtrg_status xtrg_cross_product(xtrg_ctx* ctx, const void* ckpt_a, size_t bytes_a,
+                                          const void* ckpt_b, size_t bytes_b) {
+  if (!ctx || !ckpt_a || !ckpt_b) return XTRG_EINVAL;
+  CkptHeader ha, hb;
+  TRY(load_checkpoint(ctx, ckpt_a, bytes_a, ctx->rho, &ha));
+  ctx->have_rho = false;   // rho now holds factor a only
+  TRY(load_checkpoint(ctx, ckpt_b, bytes_b, ctx->Y, &hb));
+  ctx->use_mixed = false;
+  TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, ctx->C));
+  TRY(compress(ctx, ctx->rho, ctx->Y, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+  double lns = 0.0;
+  TRY(normalize(ctx, ctx->C, &lns));
+  std::swap(ctx->rho, ctx->C);
+  ctx->lnc = ha.lnc + hb.lnc + lns;
+  ctx->beta = ha.beta + hb.beta;
+  ctx->have_rho = true;
+  ctx->rho_canonical = true;
   return XTRG_OK;
 }
 

@@ -17,14 +17,14 @@ class XTRG:
 
     def __init__(self, H_dims, H_sites, tau0, dstar, sweeps=4, order=4, init_sweeps=None,
                  prec="fp64", beta_switch=0.0, svd_rel_tol=1e-15, device="cuda:0", stream=None,
-                 keep_parts=True):
+                 keep_parts=True, orth_block=0):
         if not torch.cuda.is_available():
             raise RuntimeError("the XTRG engine needs a CUDA device")
         self.L = len(H_sites)
         self.device = torch.device(device)
         self._H = _lib.MpoArgs(H_dims, H_sites)
         self.cfg = _lib.make_config(tau0, order, dstar, sweeps, init_sweeps, prec, beta_switch,
-                                    svd_rel_tol, keep_parts)
+                                    svd_rel_tol, keep_parts, orth_block)
         nbytes = _lib.xtrg_workspace_bytes(self._H, self.cfg)
         if nbytes == 0:
             raise _lib.XtrgError(_lib.XTRG_EINVAL, "bad Hamiltonian or configuration")
@@ -58,6 +58,44 @@ class XTRG:
 
     def observables(self):
         return _lib.xtrg_observables(self.ctx)
+
+    def settn_step(self, dtau, order):
+        """rho(beta) -> rho(beta + dtau) by the pointwise-Taylor series of
+        Eq. Tay to the given order (FP64; see xtrg_settn_step)."""
+        import torch
+        n = _lib.xtrg_settn_workspace_bytes(self.ctx, order)
+        buf = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        _lib.xtrg_settn_step(self.ctx, dtau, order, ptr, n)
+        del buf
+
+    def run_settn(self, n_steps, order):
+        """init, then n_steps pointwise-Taylor steps along tau_n = 2^n tau0
+        (dtau = tau_n); one observables row per grid point."""
+        self.init()
+        rows = [self.observables()]
+        for _ in range(n_steps):
+            self.settn_step(rows[-1]["beta"], order)
+            rows.append(self.observables())
+        return rows
+
+    def expectation(self, dims, sites):
+        """<O> = Tr(O rho)/Tr rho for an operator MPO (bond dims, sites)."""
+        return _lib.xtrg_expectation(self.ctx, _lib.MpoArgs(dims, sites))
+
+    def binder_ratio(self):
+        """U_4 = <M^2>^2 / <M^4> with M = S^z_tot (Sec. IV D, Eq. Binder)."""
+        from .hamiltonians import magnetization_power
+        m2 = self.expectation(*magnetization_power(self.L, 2))
+        return m2 * m2 / self.expectation(*magnetization_power(self.L, 4))
+
+    def cross_product(self, ckpt_a, ckpt_b):
+        """Make rho_a rho_b (two buffers from ``checkpoint``) the current
+        state: rho at beta_a + beta_b (Sec. II B, after Eq. zshift)."""
+        pa = (ckpt_a.data_ptr() + 255) // 256 * 256
+        pb = (ckpt_b.data_ptr() + 255) // 256 * 256
+        _lib.xtrg_cross_product(self.ctx, pa, ckpt_a.data_ptr() + ckpt_a.numel() - pa,
+                                pb, ckpt_b.data_ptr() + ckpt_b.numel() - pb)
 
     def entanglement(self):
         """MPO entanglement S_E of the current rho at bonds 1..L-1 (Eq. purif)."""

@@ -11,6 +11,8 @@ site keeps the "ready" row and the last site the "done" column.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 _I = np.eye(2)
@@ -109,4 +111,29 @@ def xxz_bonds_mpo(N: int, bonds):
                 Wt[a, :, :, right["done"]] += g * partner[o]
         sites.append(Wt)
     dims = [1] + [len(c) for c in cuts] + [1]
+    return dims, sites
+
+
+def magnetization_power(L: int, p: int):
+    """MPO of (S^z_tot)^p, S^z_tot = sum_i S^z_i, with bond dimension p + 1
+    (the D = 3 and D = 5 forms of p = 2 and 4 that the Binder ratio of
+    Sec. IV D, Eq. Binder, needs).  Multinomial expansion: the bond state k
+    counts the power collected so far; site tensor W[k][k'] = (S^z)^(k'-k) /
+    (k'-k)! for k' >= k, the first site starts at k = 0 and carries the
+    factor p!, the last ends at k' = p.  Returns (bond_dims, sites)."""
+    if L < 2 or p < 1:
+        raise ValueError("need L >= 2 and p >= 1")
+    W = np.zeros((p + 1, 2, 2, p + 1))
+    for k in range(p + 1):
+        for k2 in range(k, p + 1):
+            W[k, :, :, k2] = np.linalg.matrix_power(_SZ, k2 - k) / math.factorial(k2 - k)
+    sites = []
+    for i in range(L):
+        w = W
+        if i == 0:
+            w = math.factorial(p) * W[0:1]
+        if i == L - 1:
+            w = w[:, :, :, p:p + 1]
+        sites.append(np.ascontiguousarray(w))
+    dims = [1] + [p + 1] * (L - 1) + [1]
     return dims, sites

@@ -43,6 +43,13 @@ def test_workspace_bytes_and_input_checks(lib):
     # larger D* needs more memory; bad configs give 0 bytes
     assert lib.xtrg_workspace_bytes(H, lib.make_config(2 ** -10, 4, 512, 4)) > n
     assert lib.xtrg_workspace_bytes(H, lib.make_config(2 ** -10, 4, 0, 4)) == 0
+    # the orthonormalisation block width: 0 (default) or 32..256 in steps of 32
+    for ob in (32, 96, 256):
+        assert lib.xtrg_workspace_bytes(H, lib.make_config(2 ** -10, 4, 256, 4, prec="bf16x6",
+                                                           orth_block=ob)) > 0
+    for ob in (-32, 16, 48, 288):
+        assert lib.xtrg_workspace_bytes(H, lib.make_config(2 ** -10, 4, 256, 4, prec="bf16x6",
+                                                           orth_block=ob)) == 0
     bad = lib.MpoArgs([2] + dims[1:], sites)
     assert lib.xtrg_workspace_bytes(bad, cfg) == 0
     # create rejects a NULL workspace before any device call
@@ -55,8 +62,11 @@ def test_workspace_bytes_and_input_checks(lib):
     assert e.value.status == lib.XTRG_ENOMEM
 
 
-@pytest.mark.parametrize("L,dstar", [(2, 1), (4, 16), (8, 256), (64, 256), (10, 3)])
-def test_workspace_plan_covers_every_buffer(lib, L, dstar):
+@pytest.mark.parametrize("L,dstar,prec", [(2, 1, "fp64"), (4, 16, "fp64"), (8, 256, "fp64"),
+                                          (64, 256, "fp64"), (10, 3, "fp64"), (8, 256, "bf16x6"),
+                                          (64, 256, "bf16x6"), (10, 320, "bf16x6"),
+                                          (12, 1024, "bf16x3")])
+def test_workspace_plan_covers_every_buffer(lib, L, dstar, prec):
     """With exactly xtrg_workspace_bytes() the carving of every buffer fits:
     on a machine without a GPU, create then fails at its first device copy
     (XTRG_ECUDA), never at carving (XTRG_ENOMEM)."""
@@ -66,7 +76,7 @@ def test_workspace_plan_covers_every_buffer(lib, L, dstar):
     from paper_1801_00142_gb300.hamiltonians import xxz_chain
     dims, sites = xxz_chain(L)
     H = lib.MpoArgs(dims, sites)
-    cfg = lib.make_config(2 ** -10, 4, dstar, 2)
+    cfg = lib.make_config(2 ** -10, 4, dstar, 2, prec=prec)
     n = lib.xtrg_workspace_bytes(H, cfg)
     with pytest.raises(lib.XtrgError) as e:
         lib.xtrg_create(H, cfg, 1 << 20, n, 0)

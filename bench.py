@@ -282,6 +282,9 @@ def run_native(args):
         cur["beta"] = o["beta"]
         return o
 
+    # a step is the doubling and the thermodynamics of Eq. ThermalQuan; the
+    # FP64 Hermiticity diagnostic is taken once, on the last state (below)
+    eng.set_herm_check(False)
     for _ in range(args.warmup):
         rows_sched.append(step())
     clocks = ClockSampler(local)
@@ -342,6 +345,8 @@ def run_native(args):
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / max(1, args.steps)
 
+    eng.set_herm_check(True)
+    herm_last = eng.observables()
     fp64 = None
     if args.prec != "fp64" and not args.no_fp64_arm and rank == 0:
         fp64 = fp64_arm(XTRG, host0, dev)
@@ -410,8 +415,12 @@ def run_native(args):
            "tc_gemm_ms_per_step": tc_ms / n_cycle,
            "orth_cluster_calls": s1["orth_cluster_calls"] - s0["orth_cluster_calls"],
            "orth_fallbacks": s1["orth_fallbacks"] - s0["orth_fallbacks"],
+           "orth_full_second_pass": s1["orth_full_second_pass"] - s0["orth_full_second_pass"],
            "fp64_arm": fp64,
-           "observables_last": {k: rows[-1][k] for k in ("beta", "lnZ", "f", "u", "max_bond")}}
+           "observables_last": {k: rows[-1][k] for k in ("beta", "lnZ", "f", "u", "max_bond")},
+           "herm_defect_last": {"beta": herm_last["beta"], "herm_defect": herm_last["herm_defect"],
+                                "note": "||rho - rho^T||_F / ||rho||_F of the state after the e2e "
+                                        "leg (FP64 transfers), taken outside the timed steps"}}
     if fp64 and fp64.get("ms_per_step"):
         out["fp64_ms_per_step"] = fp64["ms_per_step"]
         out["speedup_vs_fp64"] = fp64["ms_per_step"] / (ms / args.steps)
@@ -469,10 +478,11 @@ def fp64_arm(XTRG, host_state, dev):
 def run_gemm_microbench(args):
     """The tensor-core contraction primitive alone at the C_E shape of a
     saturated two-site update (M = N = 4 D*, K = D*^2, 3 planes, 6 products,
-    the split-K the engine picks for it), through xtrg_tc_gemm: CUDA events
-    around the GEMM kernel's launches (the plane conversions of the FP64
-    inputs are outside the events).  One JSON line; used for the roofline and
-    for small profiler captures of that launch."""
+    the split-K given), through xtrg_tc_gemm: CUDA events around whole calls
+    (BF16 plane conversion of the FP64 inputs, the GEMM kernel, the FP64
+    split-K sum; the engine's own C_E reads planes that are already
+    converted, so its rate is the kernel's).  One JSON line; used for small
+    profiler captures of the GEMM launch, whose kernel time ncu reports."""
     import torch
     from paper_1801_00142_gb300 import _lib
     D = W.dstar

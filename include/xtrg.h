@@ -103,7 +103,8 @@ typedef struct {
   double trunc_err;     /* largest discarded weight of the last sweep          */
   double herm_defect;   /* Hermiticity defect ||rho - rho^T||_F / ||rho||_F of the
                            stored rho (Sec. II B); FP64 transfers, resolved down
-                           to ~1.5e-8 (it is a square root of a difference)     */
+                           to ~1.5e-8 (it is a square root of a difference); NaN
+                           when switched off (xtrg_set_herm_check)               */
   int max_bond;         /* largest bond dimension of the current rho          */
   int n_doublings;      /* doublings done since xtrg_init                     */
 } xtrg_obs;
@@ -125,7 +126,13 @@ xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* H, const xtrg_config* cf
 xtrg_status xtrg_init(xtrg_ctx* ctx);
 
 /* One doubling: rho <- compress(rho^T rho) with cfg.sweeps full sweeps,
- * normalised; beta <- 2 beta (Eq. rho:scale2). */
+ * normalised; beta <- 2 beta (Eq. rho:scale2).  On the tensor-core path the
+ * sweeps take every decision on the device (the exact-split fallback
+ * included) and the host reads the product's results once at its end; once
+ * the bonds are saturated, the device work of a doubling is captured as a
+ * CUDA graph (one per buffer parity) and later doublings replay it
+ * (environment XTRG_NO_GRAPHS=1 turns this off; so do profiling and
+ * XTRG_DEBUG=1).  A replay computes the same as a direct run. */
 xtrg_status xtrg_double(xtrg_ctx* ctx);
 
 /* Pointwise-Taylor SETTN step (Sec. II C, Eq. Tay, Fig. SETTNAlg(b)), the
@@ -218,10 +225,18 @@ typedef struct {
   double fp64_env_pass_ms;   /* device time of the FP64-path initial right environments (profiling) */
   long long orth_fallbacks;  /* tensor-core truncations whose CholeskyQR2 broke down and were
                                 orthonormalised by block Gram-Schmidt instead (this context) */
+  long long orth_full_second_pass; /* tensor-core truncations whose first CholeskyQR pass left
+                                the basis too far from orthonormal for the first-order second
+                                pass, so the full second pass ran (this context) */
+  long long orth_deflated_columns; /* columns the first CholeskyQR pass dropped as numerically
+                                dependent on the columns before them (this context) */
+  long long graph_captures;  /* tensor-core doublings captured as a CUDA graph (this context) */
+  long long graph_replays;   /* tensor-core doublings run by replaying a captured graph */
 } xtrg_stats;
 
 /* Counters since creation (kernel_launches: since the library was loaded).
- * Synchronises the context's stream (orth_fallbacks is counted on the device). */
+ * Synchronises the context's stream (orth_fallbacks, orth_full_second_pass and
+ * orth_deflated_columns are counted on the device). */
 xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* out);
 
 /* on != 0: time every tensor-core GEMM launch, every tensor-core truncation,
@@ -229,6 +244,17 @@ xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* out);
  * with CUDA events on the context's stream (adds event records; results are
  * resolved at the end of each product, which then synchronises). */
 xtrg_status xtrg_set_profiling(xtrg_ctx* ctx, int on);
+
+/* The Hermiticity diagnostic of xtrg_observables: on = 1 (the default)
+ * computes herm_defect (FP64 transfer contractions of ||rho||_F^2 and
+ * Tr(rho rho), about 16 D^3 flops per site each); 0 leaves it NaN and the
+ * thermodynamics (ln Z, f, u, c) unchanged. */
+xtrg_status xtrg_set_herm_check(xtrg_ctx* ctx, int on);
+
+/* Graph capture of saturated tensor-core doublings (see xtrg_double): on = 1
+ * (the default) allows it, 0 runs every doubling directly and drops the
+ * graphs captured so far. */
+xtrg_status xtrg_set_graphs(xtrg_ctx* ctx, int on);
 
 /* The tensor-core contraction primitive behind the XTRG_BF16X* modes, exposed
  * on its own: C[b] = A[b] * B[b]^T for row-major FP64 device arrays

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "XTRG_OK", 1: "XTRG_EINVAL", 2: "XTRG_ENOMEM", 3: "XTRG_ECUDA
 # every exported symbol the header declares
 SYMBOLS = ["xtrg_workspace_bytes", "xtrg_create", "xtrg_init", "xtrg_double", "xtrg_trace",
            "xtrg_observables", "xtrg_get_state", "xtrg_set_state", "xtrg_get_stats",
-           "xtrg_set_profiling",
+           "xtrg_set_profiling", "xtrg_set_graphs", "xtrg_set_herm_check",
            "xtrg_last_error", "xtrg_destroy", "xtrg_tc_gemm_workspace_bytes", "xtrg_tc_gemm",
            "xtrg_tc_gemm_static", "xtrg_batch_plan", "xtrg_batch_run", "xtrg_checkpoint_bytes",
            "xtrg_checkpoint_save", "xtrg_checkpoint_load", "xtrg_entanglement",
@@ -60,7 +60,10 @@ class xtrg_stats(C.Structure):
                 ("kernel_launches", C.c_longlong), ("exact_split_fallbacks", C.c_longlong),
                 ("split_ms", C.c_double), ("orth_cluster_calls", C.c_longlong),
                 ("fp64_update_ms", C.c_double), ("fp64_updates_timed", C.c_longlong),
-                ("fp64_env_pass_ms", C.c_double), ("orth_fallbacks", C.c_longlong)]
+                ("fp64_env_pass_ms", C.c_double), ("orth_fallbacks", C.c_longlong),
+                ("orth_full_second_pass", C.c_longlong), ("orth_deflated_columns", C.c_longlong),
+                ("graph_captures", C.c_longlong),
+                ("graph_replays", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +102,10 @@ def _load():
     lib.xtrg_get_stats.argtypes = [P, C.POINTER(xtrg_stats)]
     lib.xtrg_set_profiling.restype = C.c_int
     lib.xtrg_set_profiling.argtypes = [P, C.c_int]
+    lib.xtrg_set_graphs.restype = C.c_int
+    lib.xtrg_set_graphs.argtypes = [P, C.c_int]
+    lib.xtrg_set_herm_check.restype = C.c_int
+    lib.xtrg_set_herm_check.argtypes = [P, C.c_int]
     lib.xtrg_batch_plan.restype = C.c_int
     lib.xtrg_batch_plan.argtypes = [C.c_int, C.POINTER(xtrg_mpo), C.POINTER(xtrg_config),
                                     C.c_size_t, C.c_int, C.POINTER(C.c_int),
@@ -268,6 +275,14 @@ def xtrg_get_stats(ctx) -> dict:
 
 def xtrg_set_profiling(ctx, on):
     _check(ctx, LIB.xtrg_set_profiling(ctx, 1 if on else 0))
+
+
+def xtrg_set_graphs(ctx, on):
+    _check(ctx, LIB.xtrg_set_graphs(ctx, 1 if on else 0))
+
+
+def xtrg_set_herm_check(ctx, on):
+    _check(ctx, LIB.xtrg_set_herm_check(ctx, 1 if on else 0))
 
 
 def xtrg_tc_gemm_workspace_bytes(M, N, K, batch, planes, splitk) -> int:

@@ -8,7 +8,12 @@
 // Number of kernels this library has launched (all contexts, all streams);
 // every launch site calls note_launch().
 extern unsigned long long g_xtrg_launches;
-static inline void note_launch() { __atomic_add_fetch(&g_xtrg_launches, 1ull, __ATOMIC_RELAXED); }
+// launches made by the calling host thread (a graph capture's own count)
+extern thread_local unsigned long long t_xtrg_launches;
+static inline void note_launch() {
+  __atomic_add_fetch(&g_xtrg_launches, 1ull, __ATOMIC_RELAXED);
+  ++t_xtrg_launches;
+}
 
 // One-time set-up per device (kernel attributes, SM counts, occupancy): the
 // first call on a device runs make(dev) with that device current and keeps
@@ -105,6 +110,22 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
                           const SvdBuffers& buf, cudaStream_t st, SvdResult* res,
                           bool* converged);
 
+// The same split decided on the device, with no host read: the kernel runs
+// only if *run_if > thresh (or *run_if is not finite) and keeps exactly
+// min(kcap, m, n) columns (numerically zero ones included, as zero columns
+// of the orthonormal factor).  It then raises acc->disc_max to its
+// discarded weight (non-negative doubles, compared by bit pattern), counts
+// itself in acc->runs and records a timeout (1) or a sweep limit (2) in
+// acc->status (maximum).  Buffers of acc are device memory.
+struct SvdDeviceAcc {
+  double* disc_max;
+  unsigned long long* runs;
+  int* status;
+};
+cudaError_t svd_split_f64_if(const double* M, int m, int n, int kcap, SplitMode mode,
+                             double* left, double* right, const SvdBuffers& buf, cudaStream_t st,
+                             const double* run_if, double thresh, const SvdDeviceAcc& acc);
+
 // ---------------------------------------------------------------- MPO kernels
 cudaError_t mpo_exact_product(const double* A, int la, int ra, const double* B, int lb, int rb,
                               double* G, cudaStream_t st);
@@ -113,4 +134,6 @@ cudaError_t mpo_direct_sum_site(const double* P, int pl, int pr, double alpha, c
 cudaError_t dev_fill(double* p, double v, long long n, cudaStream_t st);
 cudaError_t dev_scale(double* p, double v, long long n, cudaStream_t st);
 cudaError_t dev_sumsq(const double* p, long long n, double* out, cudaStream_t st);
+// p *= 1 / sqrt(*ss) (ss: device scalar), unless *ss is not positive and finite
+cudaError_t dev_scale_rsqrt(double* p, const double* ss, long long n, cudaStream_t st);
 cudaError_t dev_identity_site(double* p, cudaStream_t st);

@@ -4,6 +4,7 @@
 #include "common.cuh"
 
 unsigned long long g_xtrg_launches = 0;
+thread_local unsigned long long t_xtrg_launches = 0;
 
 namespace {
 
@@ -86,6 +87,16 @@ __global__ void scale_kernel(double* p, double v, long long n) {
     p[e] *= v;
 }
 
+// p *= 1 / sqrt(*ss) if *ss is positive and finite (else p is left as it is)
+__global__ void scale_rsqrt_kernel(double* p, const double* __restrict__ ss, long long n) {
+  const double v = *ss;
+  if (!(v > 0.0) || !isfinite(v)) return;
+  const double f = 1.0 / sqrt(v);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    p[e] *= f;
+}
+
 // single-CTA sum of squares (the tensors reduced here are small: one site)
 __global__ void sumsq_kernel(const double* __restrict__ p, long long n, double* out) {
   __shared__ double red[32];
@@ -136,6 +147,12 @@ cudaError_t dev_fill(double* p, double v, long long n, cudaStream_t st) {
 cudaError_t dev_scale(double* p, double v, long long n, cudaStream_t st) {
   note_launch();
   scale_kernel<<<grid_for(n), 256, 0, st>>>(p, v, n);
+  return cudaGetLastError();
+}
+
+cudaError_t dev_scale_rsqrt(double* p, const double* ss, long long n, cudaStream_t st) {
+  note_launch();
+  scale_rsqrt_kernel<<<grid_for(n), 256, 0, st>>>(p, ss, n);
   return cudaGetLastError();
 }
 

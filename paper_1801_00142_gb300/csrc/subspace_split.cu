@@ -677,30 +677,39 @@ __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // shared memory of the factor kernel: the packed lower triangle, the
 // transposed panel copy Pt[32][MAX_K], the scaling and the reciprocal pivots
+constexpr int CQ_LD = 36;   // row stride of the factored diagonal block copy (16-byte rows)
+
 size_t cholqr_factor_smem(int k) {
   const size_t packed = ((size_t)k * (k + 1) / 2 + 3) / 4 * 4;
-  return (packed + (size_t)32 * MAX_K + 2 * MAX_K) * 4;
+  return (packed + (size_t)32 * MAX_K + 32 * CQ_LD + 2 * MAX_K) * 4;
 }
 
 // G (k x k FP32 row-major, symmetric; lower triangle read) -> Lout (packed
 // lower Cholesky factor of D G D), dout (the scaling d_j; 0 for a dead
 // column), linv_out (1 / L_jj, 0 for a dead column); *flag = 1 if a live
-// scaled pivot falls below tau (never cleared here).  Right-looking, 32-wide
+// scaled pivot falls below tau (never cleared here), or, with deflate set,
+// that column is dropped as dead instead (its part orthogonal to the columns
+// before it is below sqrt(tau) of its norm: numerically dependent) and
+// counted in flag[4].  Right-looking, 32-wide
 // panels: the diagonal block in registers of warp 0 (lane = row, shuffles),
 // the rows below it one per thread against that block, then the trailing
 // update in 4 x 4 register blocks from the transposed panel copy (float4
-// reads, conflict-free).
+// reads, conflict-free).  With run_if set, runs only if *run_if != 0 and
+// *flag == 0.
 __global__ void __launch_bounds__(CQ_NT, 1)
-    cholqr_factor(const float* __restrict__ G, int k, float tau, float* __restrict__ Lout,
-                  float* __restrict__ dout, float* __restrict__ linv_out, int* flag) {
+    cholqr_factor(const float* __restrict__ G, int k, float tau, int deflate,
+                  float* __restrict__ Lout, float* __restrict__ dout, float* __restrict__ linv_out,
+                  int* flag, const int* run_if) {
+  if (run_if && (*run_if == 0 || *flag)) return;
   extern __shared__ __align__(16) float cq[];
   const int np = k * (k + 1) / 2;
   float* A = cq;                                    // packed lower triangle
   float* Pt = cq + ((np + 3) / 4 * 4);              // panel, transposed: Pt[t * MAX_K + row]
-  float* d = Pt + 32 * MAX_K;                       // scaling
+  float* Ld = Pt + 32 * MAX_K;                      // factored diagonal block, Ld[r * CQ_LD + c]
+  float* d = Ld + 32 * CQ_LD;                       // scaling
   float* li = d + MAX_K;                            // 1 / L_jj
   __shared__ float red[32];
-  __shared__ int bad;
+  __shared__ int bad, ndefl;
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   float gm = 0.f;
   for (int j = tid; j < k; j += CQ_NT) {
@@ -709,7 +718,10 @@ __global__ void __launch_bounds__(CQ_NT, 1)
   }
   for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
   if (lane == 0) red[warp] = gm;
-  if (tid == 0) bad = 0;
+  if (tid == 0) {
+    bad = 0;
+    ndefl = 0;
+  }
   __syncthreads();
   if (tid < 32) {
     float v = tid < CQ_NT / 32 ? red[tid] : 0.f;
@@ -746,12 +758,18 @@ __global__ void __launch_bounds__(CQ_NT, 1)
           const float piv = __shfl_sync(0xffffffffu, r[j], j);
           const bool dead = d[p0 + j] == 0.f;
           const bool broke = !dead && !(piv > tau);
-          const float ljj = (dead || broke) ? 1.f : sqrtf(piv);
-          const float inv = (dead || broke) ? 0.f : 1.f / ljj;
+          // 1 / L_jj by the approximate reciprocal square root (a few ulp;
+          // the second pass absorbs it) to keep the pivot chain short
+          const float rs = rsqrtf(piv);
+          const float ljj = (dead || broke) ? 1.f : piv * rs;
+          const float inv = (dead || broke) ? 0.f : rs;
           if (lane == j) {
             r[j] = ljj;
             li[p0 + j] = inv;
-            if (broke) bad = 1;
+            if (broke) {
+              if (deflate) ++ndefl;
+              else bad = 1;
+            }
           }
           if (lane > j) r[j] *= inv;
           // trailing part of the block: r[c] -= L_lane,j L_c,j for j < c <= lane
@@ -765,22 +783,35 @@ __global__ void __launch_bounds__(CQ_NT, 1)
         }
       }
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
+      for (int c = 0; c < 32; ++c) {
         if (lane < pw && c <= lane) A[pk(p0 + lane, p0 + c)] = r[c];
+        Ld[lane * CQ_LD + c] = (lane < pw && c <= lane) ? r[c] : 0.f;
+      }
     }
     __syncthreads();
-    // (b) rows below the block: L_ip = A_ip L_pp^{-T}, one thread per row
+    // (b) rows below the block: L_ip = A_ip L_pp^{-T}, one thread per row;
+    // the rows of L_pp are read as float4 broadcasts and each dot product
+    // runs in four partial sums (short dependency chains)
     for (int i = p0 + pw + tid; i < k; i += CQ_NT) {
       float x[32];
       const int base = pk(i, p0);
 #pragma unroll
       for (int t = 0; t < 32; ++t) {
         if (t < pw) {
-          float v = A[base + t];
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (q < t) v -= x[q] * A[pk(p0 + t, p0 + q)];
-          x[t] = v * li[p0 + t];
+          for (int q4 = 0; q4 < 8; ++q4) {
+            if (4 * q4 < t) {
+              const float4 l = *reinterpret_cast<const float4*>(Ld + t * CQ_LD + 4 * q4);
+              // entries q >= t of row t are zero in Ld (and x[q] for q >= t
+              // is not yet defined): only q < t is taken
+              s4[0] = fmaf(x[4 * q4], l.x, s4[0]);
+              if (4 * q4 + 1 < t) s4[1] = fmaf(x[4 * q4 + 1], l.y, s4[1]);
+              if (4 * q4 + 2 < t) s4[2] = fmaf(x[4 * q4 + 2], l.z, s4[2]);
+              if (4 * q4 + 3 < t) s4[3] = fmaf(x[4 * q4 + 3], l.w, s4[3]);
+            }
+          }
+          x[t] = (A[base + t] - ((s4[0] + s4[1]) + (s4[2] + s4[3]))) * li[p0 + t];
         }
       }
 #pragma unroll
@@ -806,24 +837,14 @@ __global__ void __launch_bounds__(CQ_NT, 1)
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        // i0, c0 are multiples of 4 below MAX_K: whole float4 reads.  Rows
+        // of Pt past k hold stale values; they only reach the entries of acc
+        // with i >= k or c >= k, which are not stored.
+#pragma unroll 8
         for (int t = 0; t < pw; ++t) {
-          float pi[4], pc[4];
-          // i0, c0 are multiples of 4 past a 32-aligned panel start: whole
-          // float4 reads unless the block runs past k
-          if (i0 + 3 < k) {
-            const float4 v = *reinterpret_cast<const float4*>(Pt + t * MAX_K + i0);
-            pi[0] = v.x; pi[1] = v.y; pi[2] = v.z; pi[3] = v.w;
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) pi[u] = (i0 + u < k) ? Pt[t * MAX_K + i0 + u] : 0.f;
-          }
-          if (c0 + 3 < k) {
-            const float4 v = *reinterpret_cast<const float4*>(Pt + t * MAX_K + c0);
-            pc[0] = v.x; pc[1] = v.y; pc[2] = v.z; pc[3] = v.w;
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) pc[u] = (c0 + u < k) ? Pt[t * MAX_K + c0 + u] : 0.f;
-          }
+          const float4 a = *reinterpret_cast<const float4*>(Pt + t * MAX_K + i0);
+          const float4 b = *reinterpret_cast<const float4*>(Pt + t * MAX_K + c0);
+          const float pi[4] = {a.x, a.y, a.z, a.w}, pc[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -846,19 +867,22 @@ __global__ void __launch_bounds__(CQ_NT, 1)
     linv_out[j] = li[j];
   }
   if (tid == 0 && bad) atomicExch(flag, 1);
+  if (tid == 0 && ndefl) atomicAdd(flag + 4, ndefl);
 }
 
 // U[r] = (Y[r] o d) L^{-T} for every row r (one warp per row; rows ldy / ldu
 // apart, so a column block of a wider matrix works in place): with u L^T = z,
 // u_j = (z_j - sum_{i<j} u_i L_ji) / L_jj, in blocks of 32 columns (earlier
 // blocks first, then a sequential solve inside the block).  Does nothing if
-// *flag is set (the fast path broke down).
+// *flag is set (the fast path broke down) or, with run_if set, if *run_if is
+// 0.  U may be Y itself (ldu = ldy): each row is read by the lanes that
+// write it, column j before U[r][j].
 __global__ void __launch_bounds__(CQ_SOLVE_NT)
-    cholqr_solve(const float* __restrict__ Y, long long ldy, int rows, int k,
+    cholqr_solve(const float* Y, long long ldy, int rows, int k,
                  const float* __restrict__ Lp, const float* __restrict__ dv,
                  const float* __restrict__ linv, const int* __restrict__ flag,
-                 float* __restrict__ U, long long ldu) {
-  if (*flag) return;
+                 const int* __restrict__ run_if, float* U, long long ldu) {
+  if (*flag || (run_if && *run_if == 0)) return;
   extern __shared__ __align__(16) float Ls[];
   const int np = k * (k + 1) / 2;
   for (int e = threadIdx.x; e < np; e += CQ_SOLVE_NT) Ls[e] = Lp[e];
@@ -913,6 +937,7 @@ cudaError_t block_cgs(float* Y, int rows, int k, const SubspaceBuffers& b, cudaS
     note_launch();
     if (cudaLaunchKernelEx(&cfg, orth_cluster, ca) == cudaSuccess) {
       __atomic_add_fetch(&g_orth_cluster_calls, 1ull, __ATOMIC_RELAXED);
+      ++t_orth_cluster_calls;
       return cudaSuccess;
     }
     // the cluster could not be launched: use the grid-wide kernel from now on
@@ -973,12 +998,12 @@ cudaError_t cholqr2_block(float* Yb, long long ldy, int rows, int w, float* tmp,
     RET(tc_product(f32_view(src, idx_plain(1), idx_plain(lds)),
                    f32_view(src, idx_plain(1), idx_plain(lds)), w, w, rows, b.out, w, b, st));
     note_launch();
-    cholqr_factor<<<1, CQ_NT, fsm, st>>>(b.out, w, pass == 0 ? 1e-6f : 0.25f, b.chol_L, b.chol_d,
-                                         b.chol_li, b.chol_flag);
+    cholqr_factor<<<1, CQ_NT, fsm, st>>>(b.out, w, pass == 0 ? 1e-6f : 0.25f, pass == 0 ? 1 : 0,
+                                         b.chol_L, b.chol_d, b.chol_li, b.chol_flag, nullptr);
     RET(cudaGetLastError());
     note_launch();
     cholqr_solve<<<grid, CQ_SOLVE_NT, ssm, st>>>(src, lds, rows, w, b.chol_L, b.chol_d, b.chol_li,
-                                                 b.chol_flag, dst, ldd);
+                                                 b.chol_flag, nullptr, dst, ldd);
     RET(cudaGetLastError());
     src = tmp;
     lds = w;
@@ -1001,24 +1026,122 @@ __global__ void subtract_block_kernel(float* __restrict__ Yb, long long ldy,
   }
 }
 
-// Y (rows x k, FP32) <- an orthonormal basis of its columns.  Up to one
-// column block (k <= b.orth_block): scaled CholeskyQR2 (Y -> U1 in b.Q -> Y), with
-// the block Gram-Schmidt kernels as the device-side fallback when a pass
-// breaks down (see cholqr_factor).  Wider: block classical Gram-Schmidt over
-// column blocks, each projected twice against the blocks before it on the
-// tensor cores (S = Q^T Y_b, Y_b -= Q S) and then orthonormalised by scaled
-// CholeskyQR2; a breakdown leaves Y unorthonormal, which the caller's
-// orthonormality check turns into the exact split.
-cudaError_t orthonormalise(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st) {
+// The second CholeskyQR pass to first order.  After the first pass the Gram
+// of U1 is G2 = I + E with E small; its Cholesky factor is L = I + Phi(E) +
+// O(E^2), Phi(E) the strictly lower part of E plus half its diagonal, so
+// U2 = U1 L^{-T} = U1 (I - Phi(E)^T) + O(E^2) and U2^T U2 = I + O(E^2).
+// Writes B = I - Phi(E) (k x k row-major: U2 = U1 B^T is one tensor-core
+// product); dead columns (G2_jj < 1/2, zero columns of U1) keep B's row e_j
+// and get zeros elsewhere.  If a live |E_ij| exceeds emax (or is not
+// finite), sets *need_full (and counts it in need_full[1]): the full second
+// pass runs instead.
+__global__ void cholqr_linear_kernel(const float* __restrict__ G, int k, float emax,
+                                     float* __restrict__ B, int* need_full) {
+  bool big = false;
+  const long long total = (long long)k * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(e / k), c = (int)(e % k);
+    const float gn = G[(long long)n * k + n], gc = G[(long long)c * k + c];
+    const bool ln = gn >= 0.5f, lc = gc >= 0.5f;
+    float v = 0.f;
+    if (!ln) {
+      v = (n == c) ? 1.f : 0.f;
+    } else if (lc) {
+      const float E = (n == c) ? gn - 1.f : G[e];
+      if (!(fabsf(E) <= emax)) big = true;
+      v = (n == c) ? 1.f - 0.5f * E : (n > c ? -E : 0.f);
+    }
+    B[e] = v;
+  }
+  if (__syncthreads_or(big) && threadIdx.x == 0) {
+    atomicExch(need_full, 1);
+    atomicAdd(need_full + 1, 1);
+  }
+}
+
+// dst[r][c] = src[r][c] (rows x k, contiguous) if *flag != 0
+__global__ void copy_if_flag_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                    long long n, const int* __restrict__ flag) {
+  if (*flag == 0) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+// Largest |E_ij| of the first-order second pass; above it the full second
+// CholeskyQR pass runs (the neglected O(E^2) terms stay below 1e-6).
+constexpr float CQ_LINEAR_EMAX = 1e-3f;
+
+// An orthonormal basis of the columns of Y (rows x k, FP32), written to
+// *U (b.Q or Y itself); Y and b.Q are overwritten.  Up to one column block
+// (k <= b.orth_block): scaled CholeskyQR2 with its second pass to first order
+// (Y -> U1 in place, then U2 = U1 B^T into b.Q, see cholqr_linear_kernel);
+// the full second pass runs instead when U1 is too far from orthonormal, and
+// the block Gram-Schmidt kernels when a pass breaks down (all chosen on the
+// device by flags; see cholqr_factor).  Wider: block classical Gram-Schmidt
+// over column blocks, each projected twice against the blocks before it on
+// the tensor cores (S = Q^T Y_b, Y_b -= Q S) and then orthonormalised by
+// scaled CholeskyQR2, result in Y; a breakdown leaves Y unorthonormal, which
+// the caller's orthonormality check turns into the exact split.
+cudaError_t orthonormalise(float* Y, int rows, int k, const SubspaceBuffers& b, cudaStream_t st,
+                           float** U) {
   if (k > SUBSPACE_MAX_K) return cudaErrorInvalidValue;
   RET(cholqr_setup());
+  // chol_flag: [0] breakdown, [1] breakdowns counted by the block Gram-Schmidt
+  // kernels, [2] full second pass needed, [3] full second passes counted,
+  // [4] columns dropped as numerically dependent by the first pass
   RET(cudaMemsetAsync(b.chol_flag, 0, sizeof(int), st));
+  RET(cudaMemsetAsync(b.chol_flag + 2, 0, sizeof(int), st));
   const int B = b.orth_block;
   if (B < 32 || B > MAX_K || B % 32) return cudaErrorInvalidValue;
   if (k <= B) {
-    RET(cholqr2_block(Y, k, rows, k, b.Q, b, st));
-    return block_cgs(Y, rows, k, b, st, b.chol_flag);
+    const size_t fsm = cholqr_factor_smem(k), ssm = (size_t)k * (k + 1) / 2 * 4;
+    const int wpb = CQ_SOLVE_NT / 32;
+    const int grid = (rows + wpb - 1) / wpb < 152 ? (rows + wpb - 1) / wpb : 152;
+    float* G = b.out;                          // k x k Grams
+    float* Bm = b.out + (size_t)k * k;         // k x k first-order factor
+    int* need_full = b.chol_flag + 2;
+    // pass 1: G = Y^T Y, scaled Cholesky, Y <- U1 in place (skipped on breakdown)
+    RET(tc_product(f32_view(Y, idx_plain(1), idx_plain(k)), f32_view(Y, idx_plain(1), idx_plain(k)),
+                   k, k, rows, G, k, b, st));
+    note_launch();
+    cholqr_factor<<<1, CQ_NT, fsm, st>>>(G, k, 1e-6f, 1, b.chol_L, b.chol_d, b.chol_li,
+                                         b.chol_flag, nullptr);
+    RET(cudaGetLastError());
+    note_launch();
+    cholqr_solve<<<grid, CQ_SOLVE_NT, ssm, st>>>(Y, k, rows, k, b.chol_L, b.chol_d, b.chol_li,
+                                                 b.chol_flag, nullptr, Y, k);
+    RET(cudaGetLastError());
+    // pass 2 to first order: G = U1^T U1 = I + E, b.Q <- U1 (I - Phi(E)^T)
+    RET(tc_product(f32_view(Y, idx_plain(1), idx_plain(k)), f32_view(Y, idx_plain(1), idx_plain(k)),
+                   k, k, rows, G, k, b, st));
+    note_launch();
+    cholqr_linear_kernel<<<grid_for((long long)k * k), 256, 0, st>>>(G, k, CQ_LINEAR_EMAX, Bm,
+                                                                     need_full);
+    RET(cudaGetLastError());
+    RET(tc_product(f32_view(Y, idx_plain(k), idx_plain(1)), f32_view(Bm, idx_plain(k), idx_plain(1)),
+                   rows, k, k, b.Q, k, b, st));
+    // the full second pass, only if E was too large: U1 -> b.Q
+    note_launch();
+    cholqr_factor<<<1, CQ_NT, fsm, st>>>(G, k, 0.25f, 0, b.chol_L, b.chol_d, b.chol_li,
+                                         b.chol_flag, need_full);
+    RET(cudaGetLastError());
+    note_launch();
+    cholqr_solve<<<grid, CQ_SOLVE_NT, ssm, st>>>(Y, k, rows, k, b.chol_L, b.chol_d, b.chol_li,
+                                                 b.chol_flag, need_full, b.Q, k);
+    RET(cudaGetLastError());
+    // a breakdown in either pass: block Gram-Schmidt on Y (the input, or U1
+    // after a breakdown of the second pass), copied to b.Q
+    RET(block_cgs(Y, rows, k, b, st, b.chol_flag));
+    note_launch();
+    copy_if_flag_kernel<<<grid_for((long long)rows * k), 256, 0, st>>>(Y, b.Q, (long long)rows * k,
+                                                                       b.chol_flag);
+    RET(cudaGetLastError());
+    *U = b.Q;
+    return cudaSuccess;
   }
+  *U = Y;
   for (int j0 = 0; j0 < k; j0 += B) {
     const int w = k - j0 < B ? k - j0 : B;
     float* Yb = Y + j0;
@@ -1042,6 +1165,7 @@ cudaError_t orthonormalise(float* Y, int rows, int k, const SubspaceBuffers& b, 
 }  // namespace
 
 unsigned long long g_orth_cluster_calls = 0;
+thread_local unsigned long long t_orth_cluster_calls = 0;
 
 size_t subspace_plane_elems_a(int cap) { return 3 * (size_t)(4 * cap) * tc_ld(4 * cap); }
 size_t subspace_plane_elems_b(int cap) { return 3 * (size_t)(4 * cap) * tc_ld(4 * cap); }
@@ -1052,7 +1176,7 @@ namespace {
 __global__ void orth_defect_kernel(const float* __restrict__ G, int k, double* out) {
   __shared__ float red[32];
   float mx = 0.f;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
     const int i = e / k, j = e % k;
     const float gi = G[(long long)i * k + i], gj = G[(long long)j * k + j];
     if (gi < 0.5f || gj < 0.5f) continue;
@@ -1065,7 +1189,9 @@ __global__ void orth_defect_kernel(const float* __restrict__ G, int k, double* o
   if (threadIdx.x == 0) {
     float t = 0.f;
     for (int i = 0; i < (int)(blockDim.x / 32); ++i) t = fmaxf(t, red[i]);
-    *out = (double)t;
+    // non-negative doubles order like their bit patterns (*out starts at +0)
+    atomicMax(reinterpret_cast<unsigned long long*>(out),
+              (unsigned long long)__double_as_longlong((double)t));
   }
 }
 
@@ -1073,7 +1199,8 @@ cudaError_t orth_check(const float* Q, int rows, int k, const SubspaceBuffers& b
   RET(tc_product(f32_view(Q, idx_plain(1), idx_plain(k)), f32_view(Q, idx_plain(1), idx_plain(k)),
                  k, k, rows, b.out, k, b, st));
   note_launch();
-  orth_defect_kernel<<<1, 1024, 0, st>>>(b.out, k, b.dscal + 2);
+  const int g = (k * k + 4095) / 4096;
+  orth_defect_kernel<<<g < 152 ? g : 152, 1024, 0, st>>>(b.out, k, b.dscal + 2);
   return cudaGetLastError();
 }
 
@@ -1089,10 +1216,46 @@ size_t subspace_buffer_floats(int cap) {
 
 int subspace_orth_ctas(int cap) { return (4 * cap + ROWS_PER_CTA - 1) / ROWS_PER_CTA; }
 
+namespace {
+// discarded weight 1 - ||centre||^2 / ||C_E||^2 of an accepted split
+// (orthonormality defect <= thresh) raised into *disc_max
+__global__ void split_finish_kernel(const double* __restrict__ ce_ss, const double* __restrict__ dscal,
+                                    double thresh, double* disc_max) {
+  const double tot = *ce_ss, defect = dscal[2];
+  const double disc = tot > 0.0 ? fmax(0.0, 1.0 - dscal[1] / tot) : 0.0;
+  if (defect <= thresh)
+    atomicMax(reinterpret_cast<unsigned long long*>(disc_max),
+              (unsigned long long)__double_as_longlong(disc));
+}
+
+// After the orthonormality check (G = Q^T Q): the defect is set to +inf if no
+// column of Q is live, or if a blocked orthonormalisation (which has no
+// Gram-Schmidt fallback) broke down, so that the exact split runs.
+__global__ void split_guard_kernel(const float* __restrict__ G, int k, const int* __restrict__ flag,
+                                   int blocked, double* defect) {
+  __shared__ int live;
+  if (threadIdx.x == 0) live = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x)
+    if (G[(long long)j * k + j] >= 0.5f) live = 1;
+  __syncthreads();
+  if (threadIdx.x == 0 && (!live || (blocked && *flag))) *defect = INFINITY;
+}
+
+cudaError_t split_guard(int k, const SubspaceBuffers& b, cudaStream_t st) {
+  note_launch();
+  split_guard_kernel<<<1, 256, 0, st>>>(b.out, k, b.chol_flag, k > b.orth_block ? 1 : 0,
+                                        b.dscal + 2);
+  return cudaGetLastError();
+}
+}  // namespace
+
+const double* subspace_defect(const SubspaceBuffers& b) { return b.dscal + 2; }
+
 cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
                            const double* warm, int kold, double* left, double* right,
                            unsigned long long seed, const SubspaceBuffers& b, cudaStream_t st,
-                           double* discarded, double* orth_defect) {
+                           double* disc_max, double thresh) {
   (void)CE;
   if (k > SUBSPACE_MAX_K || k > m || k > n) return cudaErrorInvalidValue;
   const double inv_mn = 1.0 / ((double)m * n);
@@ -1111,13 +1274,15 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
     add_noise_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.Y, (long long)m * k, b.ce_ss,
                                                                  inv_mn, seed + 7);
     RET(cudaGetLastError());
-    RET(orthonormalise(b.Y, m, k, b, st));
-    RET(orth_check(b.Y, m, k, b, st));
+    float* U = nullptr;
+    RET(orthonormalise(b.Y, m, k, b, st, &U));
+    RET(orth_check(U, m, k, b, st));
+    RET(split_guard(k, b, st));
     // C_i = U (m x k); C_{i+1} = U^T C_E (k x n)
     note_launch();
-    copy_f2d_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.Y, (long long)m * k, left);
+    copy_f2d_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(U, (long long)m * k, left);
     // U^T C_E (k x n): A = U^T (k rows, K = m), B = C_E^T (n rows, K = m)
-    RET(tc_product(f32_view(b.Y, idx_plain(1), idx_plain(k)), cet, k, n, m, b.out, n, b, st));
+    RET(tc_product(f32_view(U, idx_plain(1), idx_plain(k)), cet, k, n, m, b.out, n, b, st));
     note_launch();
     copy_f2d_kernel<<<grid_for((long long)k * n), 256, 0, st>>>(b.out, (long long)k * n, right);
     RET(cudaGetLastError());
@@ -1132,30 +1297,30 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
     add_noise_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(b.Y, (long long)n * k, b.ce_ss,
                                                                  inv_mn, seed + 7);
     RET(cudaGetLastError());
-    RET(orthonormalise(b.Y, n, k, b, st));
-    RET(orth_check(b.Y, n, k, b, st));
+    float* V = nullptr;
+    RET(orthonormalise(b.Y, n, k, b, st, &V));
+    RET(orth_check(V, n, k, b, st));
+    RET(split_guard(k, b, st));
     // C_{i+1} = V^T (k x n); C_i = C_E V (m x k)
     note_launch();
-    transpose_f2d_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(b.Y, n, k, right);
+    transpose_f2d_kernel<<<grid_for((long long)n * k), 256, 0, st>>>(V, n, k, right);
     // C_E V (m x k): A = C_E (m rows, K = n), B = V^T (k rows, K = n)
-    RET(tc_product(ce, f32_view(b.Y, idx_plain(1), idx_plain(k)), m, k, n, b.out, k, b, st));
+    RET(tc_product(ce, f32_view(V, idx_plain(1), idx_plain(k)), m, k, n, b.out, k, b, st));
     note_launch();
     copy_f2d_kernel<<<grid_for((long long)m * k), 256, 0, st>>>(b.out, (long long)m * k, left);
     RET(cudaGetLastError());
   }
-  // discarded weight = 1 - ||centre||^2 / ||C_E||^2; the one host read of the update
+  // ||centre||^2 for the discarded weight 1 - ||centre||^2 / ||C_E||^2
   double* centre = dir_right ? right : left;
   const long long nc = dir_right ? (long long)k * n : (long long)m * k;
   note_launch();
   sumsq_f64_kernel<<<grid_for(nc) < 304 ? grid_for(nc) : 304, 256, 0, st>>>(centre, nc,
                                                                             b.dscal + 1);
   RET(cudaGetLastError());
-  double h[3] = {0.0, 0.0, 0.0};
-  RET(cudaMemcpyAsync(h, b.ce_ss, sizeof(double), cudaMemcpyDeviceToHost, st));
-  RET(cudaMemcpyAsync(h + 1, b.dscal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  RET(cudaStreamSynchronize(st));
-  const double tot = h[0];
-  *discarded = tot > 0.0 ? fmax(0.0, 1.0 - h[1] / tot) : 0.0;
-  *orth_defect = h[2];
+  if (disc_max) {
+    note_launch();
+    split_finish_kernel<<<1, 1, 0, st>>>(b.ce_ss, b.dscal, thresh, disc_max);
+    RET(cudaGetLastError());
+  }
   return cudaSuccess;
 }

@@ -31,7 +31,8 @@ struct SubspaceBuffers {
   float* chol_L;          // w (w + 1) / 2 for a column block of width w
   float* chol_d;          // SUBSPACE_BLOCK_K
   float* chol_li;         // SUBSPACE_BLOCK_K
-  int* chol_flag;         // [0] breakdown flag of the current call, [1] count of breakdowns
+  int* chol_flag;         // [0] breakdown flag of the current call, [1] count of breakdowns,
+                          // [2] full second pass flag, [3] its count, [4] deflated columns
   int orth_block;         // column-block width of the orthonormalisation (32..SUBSPACE_BLOCK_K)
 };
 
@@ -44,8 +45,10 @@ constexpr int SUBSPACE_MAX_K = 1024;
 // Floats of chol_L (one column block).
 constexpr size_t SUBSPACE_CHOL_FLOATS = (size_t)SUBSPACE_BLOCK_K * (SUBSPACE_BLOCK_K + 1) / 2;
 
-// Orthonormalisations launched as one thread-block cluster (all contexts).
+// Orthonormalisations launched as one thread-block cluster (all contexts; and
+// by the calling host thread).
 extern unsigned long long g_orth_cluster_calls;
+extern thread_local unsigned long long t_orth_cluster_calls;
 
 // BF16 elements of pa and pb for bond capacity cap.
 size_t subspace_plane_elems_a(int cap);
@@ -62,10 +65,13 @@ int subspace_orth_ctas(int cap);
 // dir_right = 1 (left-to-right): left = U orthonormal, right = U^T C_E,
 // warm = current C_{i+1} (kold x n, orthonormal rows).  dir_right = 0:
 // right = V^T orthonormal rows, left = C_E V, warm = current C_i (m x kold).
-// *orth_defect: max |Q^T Q - I| over the live columns of the orthonormal
-// factor; the caller falls back to the exact split when it is too large.
-// Synchronises the stream once (reads the discarded weight and the defect).
+// Everything stays on the device (no host read): the orthonormality defect
+// max |Q^T Q - I| over the live columns of the orthonormal factor is left in
+// *subspace_defect(b), from which the caller's exact fallback decides on the
+// device; if disc_max is not null and the defect is <= thresh, the
+// discarded weight 1 - ||kept||^2 / ||C_E||^2 is raised into *disc_max.
 cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
                            const double* warm, int kold, double* left, double* right,
                            unsigned long long seed, const SubspaceBuffers& b, cudaStream_t st,
-                           double* discarded, double* orth_defect);
+                           double* disc_max, double thresh);
+const double* subspace_defect(const SubspaceBuffers& b);

@@ -41,6 +41,11 @@ struct SvdArgs {
   int* out;           // [0] k, [1] rank, [2] sweeps, [3] status (0 ok, 1 timeout, 2 not converged)
   double* stats;      // [0] total weight, [1] discarded fraction, [2] sigma_max,
                       // [3] ||M||_F^2 (accumulated while loading)
+  // device-decided mode (all null otherwise): run only if *run_if > thresh
+  // or is not finite; keep exactly min(kcap, ncols); report into acc
+  const double* run_if;
+  double thresh;
+  SvdDeviceAcc acc;
 };
 
 // Grid barrier with a bounded wait.  Returns false if the wait expired or
@@ -67,6 +72,7 @@ __device__ bool grid_barrier(const SvdArgs& a) {
         while (vb[1] == gen) {
           if (++it > SPIN_LIMIT || *st == 1) {
             atomicExch(a.out + 3, 1);
+            if (a.acc.status) atomicMax(a.acc.status, 1);
             ok = 0;
             break;
           }
@@ -86,6 +92,8 @@ __device__ inline double warp_sum(double v) {
 }
 
 __global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
+  // device-decided mode: every CTA leaves before the first barrier
+  if (a.run_if && *a.run_if <= a.thresh) return;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * WPB + (threadIdx.x >> 5);
   const int TW = gridDim.x * WPB;
@@ -198,6 +206,7 @@ __global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
     int cnt = 0;
     for (int j = 0; j < a.ncols; ++j) cnt += a.sig[j] > a.rel_tol * mx;
     int k = cnt < a.kcap ? cnt : a.kcap;
+    if (a.run_if) k = a.kcap < a.ncols ? a.kcap : a.ncols;
     if (k < 1) k = 1;
     double keptw = 0.0;
     for (int r = 0; r < k; ++r) { double s = a.sig[a.perm[r]]; keptw += s * s; }
@@ -208,6 +217,14 @@ __global__ void __launch_bounds__(NT) svd_persistent(SvdArgs a) {
     a.stats[0] = totw;
     a.stats[1] = totw > 0.0 ? fmax(0.0, (totw - keptw) / totw) : 0.0;
     a.stats[2] = mx;
+    if (a.run_if) {
+      if (a.acc.disc_max)
+        atomicMax(reinterpret_cast<unsigned long long*>(a.acc.disc_max),
+                  (unsigned long long)__double_as_longlong(a.stats[1]));
+      if (a.acc.runs) atomicAdd(a.acc.runs, 1ull);
+      if (a.acc.status && !converged) atomicMax(a.acc.status, 2);
+      if (a.acc.status && !isfinite(mx)) atomicMax(a.acc.status, 3);
+    }
   }
   if (!grid_barrier(a)) return;
 
@@ -260,15 +277,12 @@ SvdSetup svd_setup() {
   return s;
 }
 
-}  // namespace
-
-cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_tol, SplitMode mode,
-                          double* left, double* right, const SvdBuffers& buf, cudaStream_t st,
-                          SvdResult* res, bool* converged) {
+cudaError_t svd_launch(const double* M, int m, int n, int kcap, double rel_tol, SplitMode mode,
+                       double* left, double* right, const SvdBuffers& buf, cudaStream_t st,
+                       const double* run_if, double thresh, const SvdDeviceAcc& acc) {
   const int trans = (m < n) ? 1 : 0;
   const int len = trans ? n : m;
   const int ncols = trans ? m : n;
-  *converged = true;
   if ((size_t)len * ncols > buf.max_elems || (size_t)ncols * ncols > buf.max_elems ||
       ncols > buf.max_cols)
     return cudaErrorInvalidValue;
@@ -288,6 +302,9 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
   a.rot = buf.counter + 2;             // 3 words
   a.out = buf.kept;                    // 4 words
   a.stats = buf.stats;
+  a.run_if = run_if;
+  a.thresh = thresh;
+  a.acc = acc;
   if ((e = cudaMemsetAsync(buf.counter, 0, 8 * sizeof(int), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(buf.kept, 0, 4 * sizeof(int), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(buf.stats, 0, 4 * sizeof(double), st)) != cudaSuccess) return e;
@@ -299,9 +316,25 @@ cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_to
   if (grid < 1) grid = 1;
   void* args[] = {&a};
   note_launch();
-  if ((e = cudaLaunchCooperativeKernel((void*)svd_persistent, dim3(grid), dim3(NT), args, 0, st)) !=
-      cudaSuccess)
-    return e;
+  return cudaLaunchCooperativeKernel((void*)svd_persistent, dim3(grid), dim3(NT), args, 0, st);
+}
+
+}  // namespace
+
+cudaError_t svd_split_f64_if(const double* M, int m, int n, int kcap, SplitMode mode,
+                             double* left, double* right, const SvdBuffers& buf, cudaStream_t st,
+                             const double* run_if, double thresh, const SvdDeviceAcc& acc) {
+  if (!run_if) return cudaErrorInvalidValue;
+  return svd_launch(M, m, n, kcap, 0.0, mode, left, right, buf, st, run_if, thresh, acc);
+}
+
+cudaError_t svd_split_f64(const double* M, int m, int n, int kcap, double rel_tol, SplitMode mode,
+                          double* left, double* right, const SvdBuffers& buf, cudaStream_t st,
+                          SvdResult* res, bool* converged) {
+  *converged = true;
+  cudaError_t e = svd_launch(M, m, n, kcap, rel_tol, mode, left, right, buf, st, nullptr, 0.0,
+                             SvdDeviceAcc{nullptr, nullptr, nullptr});
+  if (e != cudaSuccess) return e;
   int out[4];
   double stats[3];
   if ((e = cudaMemcpyAsync(out, buf.kept, sizeof out, cudaMemcpyDeviceToHost, st)) != cudaSuccess)

@@ -108,7 +108,7 @@ bool plan_sizes(int L, int DH, const xtrg_config* cfg, Plan* p) {
     // when they stay resident (keep_parts)
     const size_t nparts = cfg->keep_parts ? (size_t)L : 1;
     mb += 2 * up(pl * p->m_t1 * 2) + 2 * up(nparts * pl * p->m_lp * 2);
-    mb += up(pl * p->m_ct * 2) + up(p->m_part * 4) + ALIGN;
+    mb += up(pl * p->m_ct * 2) + up(p->m_part * 4) + 2 * ALIGN;
     mb += up(subspace_buffer_floats(p->cap) * 4) + 3 * ALIGN;
     mb += up(subspace_plane_elems_a(p->cap) * 2) + up(subspace_plane_elems_b(p->cap) * 2);
     mb += 2 * up(subspace_plane_elems_a(p->cap) * 2) + ALIGN;   // C_E planes, both orientations
@@ -164,6 +164,12 @@ struct xtrg_ctx {
     std::vector<__nv_bfloat16*> lpc, rpc;
     float* part = nullptr;
     int* err = nullptr;
+    // device-side results of a product's sweeps, read once at its end:
+    // [0] largest discarded weight of the last sweep, [1] exact-split
+    // fallbacks (u64, cumulative), [2] +inf (run condition of an exact split
+    // that always runs), [3] status of the exact splits (int: 1 timeout,
+    // 2 sweep limit, 3 non-finite)
+    double* acc = nullptr;
     SubspaceBuffers sb{};
   } m;
   bool mixed_ready = false;
@@ -186,6 +192,24 @@ struct xtrg_ctx {
   long long tag_n[8] = {0};
   int cur_tag = 0;
   long long fallbacks = 0;   // tensor-core path updates that used the exact split
+  // CUDA graphs of saturated tensor-core doublings (one per buffer parity:
+  // rho and C swap after every doubling)
+  struct DoublingGraph {
+    cudaGraphExec_t exec = nullptr;
+    const double* rho0 = nullptr;   // rho's first site when captured (the parity)
+    std::vector<int> dims;          // rho's bonds when captured
+    std::vector<int> out_dims;      // C's bonds after the captured doubling
+    // host counters a replay advances by
+    long long d_updates = 0;
+    unsigned long long d_launches = 0, d_cluster = 0;
+    double d_flops_contr = 0.0, d_flops_split = 0.0;
+  };
+  std::vector<DoublingGraph> graphs;
+  cudaStream_t cap_st = nullptr;    // capture stream (created on first use)
+  std::vector<int> prev_mixed_dims;  // rho's bonds at the previous tensor-core doubling
+  bool graphs_off = false;           // disabled (XTRG_NO_GRAPHS=1) or a capture failed
+  bool herm_check = true;            // xtrg_observables computes herm_defect
+  long long graph_replays = 0, graph_captures = 0;
   std::string err;
 };
 
@@ -560,18 +584,28 @@ xtrg_status compress_sum(xtrg_ctx* ctx, std::vector<SumTerm>& terms, DevMpo& C, 
 }
 
 // ||C_0||_F for the centre site; C_0 /= s.  Returns ln s.
-xtrg_status normalize(xtrg_ctx* ctx, DevMpo& C, double* lns) {
+// Device part: s^2 = ||C_0||_F^2 into ctx->scal[0], C_0 /= s (no host read).
+xtrg_status normalize_device(xtrg_ctx* ctx, DevMpo& C) {
   const long long n = (long long)site_elems(C, 0);
   CK(dev_sumsq(C.site[0], n, ctx->scal, ctx->st));
+  CK(dev_scale_rsqrt(C.site[0], ctx->scal, n, ctx->st));
+  return XTRG_OK;
+}
+
+// Host part: reads s^2 (synchronises), *lns = ln s.
+xtrg_status normalize_finish(xtrg_ctx* ctx, double* lns) {
   double ss = 0.0;
   CK(cudaMemcpyAsync(&ss, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   if (!(ss > 0.0) || !std::isfinite(ss))
     return fail(ctx, XTRG_ENUMERIC, "norm of the compressed MPO is %g", ss);
-  const double s = std::sqrt(ss);
-  CK(dev_scale(C.site[0], 1.0 / s, n, ctx->st));
-  *lns = std::log(s);
+  *lns = std::log(std::sqrt(ss));
   return XTRG_OK;
+}
+
+xtrg_status normalize(xtrg_ctx* ctx, DevMpo& C, double* lns) {
+  TRY(normalize_device(ctx, C));
+  return normalize_finish(ctx, lns);
 }
 
 // Debug mode (environment XTRG_DEBUG=1): after each step of a product, scan
@@ -783,23 +817,56 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, const __nv_bfloat16* Lp, const __nv_bfloat16
   return XTRG_OK;
 }
 
+// Largest orthonormality defect of the subspace truncation's factor that is
+// accepted; above it the exact FP64 split runs instead.
+constexpr double ORTH_DEFECT_MAX = 1e-4;
+
+// The one host read of a tensor-core product: the bounded-wait flag of the
+// GEMMs, the largest discarded weight of the last sweep, the exact-split
+// fallbacks and their status.
+xtrg_status finish_mixed(xtrg_ctx* ctx) {
+  int h = 0;
+  double a[4];
+  CKM(cudaMemcpyAsync(&h, ctx->m.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CKM(cudaMemcpyAsync(a, ctx->m.acc, sizeof a, cudaMemcpyDeviceToHost, ctx->st));
+  CKM(cudaStreamSynchronize(ctx->st));
+  if (h) return fail(ctx, XTRG_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
+  unsigned long long runs = 0;
+  int status = 0;
+  memcpy(&runs, &a[1], sizeof runs);
+  memcpy(&status, &a[3], sizeof status);
+  ctx->fallbacks = (long long)runs;
+  if (status == 1) return fail(ctx, XTRG_ETIMEOUT, "exact split: a bounded device barrier expired");
+  if (status == 2) return fail(ctx, XTRG_ENUMERIC, "exact split: Jacobi SVD did not converge");
+  if (status == 3) return fail(ctx, XTRG_ENUMERIC, "exact split: non-finite singular value");
+  ctx->last_trunc = a[0];
+  return XTRG_OK;
+}
+
 xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
   const int L = ctx->L;
   const DevMpo& R = ctx->rho;
   const int kcap = dstar < ctx->cap ? dstar : ctx->cap;
   const bool keep = ctx->cfg.keep_parts != 0;
+  double* disc_max = ctx->m.acc;
+  const SvdDeviceAcc acc{disc_max, reinterpret_cast<unsigned long long*>(ctx->m.acc + 1),
+                         reinterpret_cast<int*>(ctx->m.acc + 3)};
+  // every decision of the sweeps is taken on the device: no host read until
+  // the end of the product
   CKM(cudaMemsetAsync(ctx->m.err, 0, sizeof(int), ctx->st));
+  CKM(cudaMemsetAsync(ctx->m.acc + 3, 0, sizeof(double), ctx->st));
   TRY(mixed_unit_env(ctx, 0));
   TRY(mixed_unit_env(ctx, L));
   for (int j = L - 1; j >= 1; --j) {
     TRY(mixed_right_part(ctx, C, j));
     TRY(mixed_env(ctx, C.site[j], C.dims[j], 4 * C.dims[j + 1], false, ctx->m.rpc[j], R.dims[j], j));
   }
-  double maxdisc = 0.0;
+  long long upd = 0;   // updates of this product (the noise seed of its truncation)
   for (int s = 0; s < sweeps; ++s) {
     const bool last = s == sweeps - 1;
+    if (last) CKM(cudaMemsetAsync(disc_max, 0, sizeof(double), ctx->st));
     for (int dir = 0; dir < 2; ++dir) {
-      for (int step = 0; step < L - 1; ++step) {
+      for (int step = 0; step < L - 1; ++step, ++upd) {
         const int i = dir == 0 ? step : L - 2 - step;
         // Left-to-right, the left half of bond i is new (environment i was
         // just rebuilt) and the right half is unchanged since it was built
@@ -813,37 +880,33 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
         // keep k = min(D*, m, n): the FP32-level C_E has no FP64-exact numerical rank
         int k = kcap < m ? kcap : m;
         k = k < n ? k : n;
-        double disc = 0.0, defect = 0.0;
-        const unsigned long long seed =
-            0x243F6A8885A308D3ull ^ ((unsigned long long)ctx->nd << 40) ^ (unsigned long long)ctx->updates;
+        const unsigned long long seed = 0x243F6A8885A308D3ull ^ (unsigned long long)upd;
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (ctx->profiling) TRY(ev_pair(ctx, TAG_SPLIT, &s0, &s1));
+        const SplitMode mode = dir == 0 ? SPLIT_RIGHT : SPLIT_LEFT;
+        const SvdDeviceAcc a{last ? acc.disc_max : nullptr, acc.runs, acc.status};
         if (k > SUBSPACE_MAX_K) {
           // wider than the blocked orthonormalisation handles: exact split
-          defect = 1.0;
-        } else if (dir == 0) {
-          CKM(subspace_split(ctx->CE, m, n, k, 1, C.site[i + 1], C.dims[i + 1], C.site[i],
-                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc, &defect));
+          CKM(svd_split_f64_if(ctx->CE, m, n, k, mode, C.site[i], C.site[i + 1], ctx->svd, ctx->st,
+                               ctx->m.acc + 2, 0.0, a));
         } else {
-          CKM(subspace_split(ctx->CE, m, n, k, 0, C.site[i], C.dims[i + 1], C.site[i],
-                             C.site[i + 1], seed, ctx->m.sb, ctx->st, &disc, &defect));
+          if (dir == 0)
+            CKM(subspace_split(ctx->CE, m, n, k, 1, C.site[i + 1], C.dims[i + 1], C.site[i],
+                               C.site[i + 1], seed, ctx->m.sb, ctx->st, a.disc_max, ORTH_DEFECT_MAX));
+          else
+            CKM(subspace_split(ctx->CE, m, n, k, 0, C.site[i], C.dims[i + 1], C.site[i],
+                               C.site[i + 1], seed, ctx->m.sb, ctx->st, a.disc_max, ORTH_DEFECT_MAX));
+          // the FP32 orthonormalisation lost orthogonality (steep or rank-
+          // deficient spectrum): the exact FP64 Jacobi split replaces it,
+          // decided on the device from the defect
+          CKM(svd_split_f64_if(ctx->CE, m, n, k, mode, C.site[i], C.site[i + 1], ctx->svd, ctx->st,
+                               subspace_defect(ctx->m.sb), ORTH_DEFECT_MAX, a));
         }
         if (s1) CKM(cudaEventRecord(s1, ctx->st));
-        if (!(defect <= 1e-4)) {
-          // the FP32 orthonormalisation lost orthogonality (steep or rank-
-          // deficient spectrum): take the exact FP64 Jacobi split instead
-          SvdResult r;
-          TRY(split(ctx, ctx->CE, m, n, k, dir == 0 ? SPLIT_RIGHT : SPLIT_LEFT, C.site[i],
-                    C.site[i + 1], &r));
-          k = r.k;
-          disc = r.discarded;
-          ctx->fallbacks++;
-        }
         C.dims[i + 1] = k;
         TRY(debug_check(ctx, "left factor", C.site[i], (long long)m * k, i));
         TRY(debug_check(ctx, "right factor", C.site[i + 1], (long long)k * n, i));
         ctx->flops_split += 2.0 * m * (double)n * k * 2 + 3.0 * (2.0 * (dir == 0 ? m : n) * k * k);
-        if (last && disc > maxdisc) maxdisc = disc;
         if (dir == 0)
           TRY(mixed_env(ctx, C.site[i], k, m, true, ctx->m.lpc[i], R.dims[i + 1], i + 1));
         else
@@ -852,12 +915,6 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
       }
     }
   }
-  int h = 0;
-  CKM(cudaMemcpyAsync(&h, ctx->m.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  CKM(cudaStreamSynchronize(ctx->st));
-  if (h) return fail(ctx, XTRG_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
-  TRY(resolve_events(ctx));
-  ctx->last_trunc = maxdisc;
   return XTRG_OK;
 }
 
@@ -1065,6 +1122,7 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
     ctx->m.Ct = (__nv_bfloat16*)carve(ctx, P * p.m_ct * 2);
     ctx->m.part = (float*)carve(ctx, p.m_part * 4);
     ctx->m.err = (int*)carve(ctx, 16);
+    ctx->m.acc = (double*)carve(ctx, 64);
     {
       const size_t c = p.cap, mm = 4 * c;
       float* f = (float*)carve(ctx, subspace_buffer_floats(p.cap) * 4);
@@ -1096,14 +1154,14 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
       ctx->m.sb.chol_L = (float*)carve(ctx, SUBSPACE_CHOL_FLOATS * 4);
       ctx->m.sb.chol_d = (float*)carve(ctx, SUBSPACE_BLOCK_K * 4);
       ctx->m.sb.chol_li = (float*)carve(ctx, SUBSPACE_BLOCK_K * 4);
-      ctx->m.sb.chol_flag = (int*)carve(ctx, 16);
+      ctx->m.sb.chol_flag = (int*)carve(ctx, 32);
       ctx->m.sb.orth_block = cfg->orth_block ? cfg->orth_block : SUBSPACE_BLOCK_K;
       ok = ok && ctx->m.sb.ce_rm && ctx->m.sb.ce_tr && ctx->m.sb.ce_ss && ctx->m.sb.chol_L &&
            ctx->m.sb.chol_d && ctx->m.sb.chol_li && ctx->m.sb.chol_flag;
       ok = ok && ctx->m.sb.dscal && ctx->m.sb.pa && ctx->m.sb.pb;
     }
     ok = ok && ctx->m.T1 && ctx->m.T1R && ctx->m.Lp && ctx->m.Rp && ctx->m.Ct && ctx->m.part &&
-         ctx->m.err;
+         ctx->m.err && ctx->m.acc;
     ctx->mixed_ready = ok;
   }
   if (!ok) {
@@ -1112,9 +1170,14 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   }
   ctx->env.resize(ctx->L + 1);
   for (int i = 0; i <= ctx->L; ++i) ctx->env[i] = envbase + (size_t)i * p.n_env;
-  if (ctx->mixed_ready && cudaMemsetAsync(ctx->m.sb.chol_flag, 0, 16, ctx->st) != cudaSuccess) {
-    delete ctx;
-    return XTRG_ECUDA;
+  if (ctx->mixed_ready) {
+    const double acc0[4] = {0.0, 0.0, INFINITY, 0.0};
+    if (cudaMemsetAsync(ctx->m.sb.chol_flag, 0, 32, ctx->st) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->m.acc, acc0, sizeof acc0, cudaMemcpyHostToDevice, ctx->st) !=
+            cudaSuccess) {
+      delete ctx;
+      return XTRG_ECUDA;
+    }
   }
   // Hamiltonian and identity sites
   for (int i = 0; i <= ctx->L; ++i) ctx->H.dims[i] = Hm->bond_dims[i];
@@ -1180,28 +1243,150 @@ extern "C" xtrg_status xtrg_init(xtrg_ctx* ctx) {
   return XTRG_OK;
 }
 
+namespace {
+
+// Device work of a tensor-core doubling from a right-canonical rho: the guess
+// C = rho, rho's operand planes, the sweeps, the normalisation of C.  No
+// host read, so it can be captured as one CUDA graph.
+xtrg_status mixed_doubling_body(xtrg_ctx* ctx) {
+  ctx->C.dims = ctx->rho.dims;
+  for (int i = 0; i < ctx->L; ++i)
+    CK(cudaMemcpyAsync(ctx->C.site[i], ctx->rho.site[i], sizeof(double) * site_elems(ctx->rho, i),
+                       cudaMemcpyDeviceToDevice, ctx->st));
+  TRY(mixed_prepare(ctx));
+  TRY(compress_mixed(ctx, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+  return normalize_device(ctx, ctx->C);
+}
+
+bool graphs_disabled_by_env() {
+  static const bool v = []() {
+    const char* e = getenv("XTRG_NO_GRAPHS");
+    return e && e[0] == '1';
+  }();
+  return v;
+}
+
+// Capture mixed_doubling_body on the context's capture stream.  On any
+// failure the capture is abandoned, graphs stay off for this context and the
+// caller runs the body directly.
+bool capture_doubling(xtrg_ctx* ctx, xtrg_ctx::DoublingGraph* g) {
+  if (!ctx->cap_st && cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->cap_st = nullptr;
+    return false;
+  }
+  cudaStream_t user = ctx->st;
+  const long long u0 = ctx->updates;
+  const unsigned long long l0 = t_xtrg_launches, c0 = t_orth_cluster_calls;
+  const double fc0 = ctx->flops_contr, fs0 = ctx->flops_split;
+  if (cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->st = ctx->cap_st;
+  const xtrg_status body = mixed_doubling_body(ctx);
+  ctx->st = user;
+  g->out_dims = ctx->C.dims;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(ctx->cap_st, &graph);
+  bool ok = body == XTRG_OK && ec == cudaSuccess && graph;
+  if (ok && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) ok = false;
+  if (graph) cudaGraphDestroy(graph);
+  // the host counters advanced while capturing; replays advance them again
+  g->d_updates = ctx->updates - u0;
+  g->d_launches = t_xtrg_launches - l0;
+  g->d_cluster = t_orth_cluster_calls - c0;
+  g->d_flops_contr = ctx->flops_contr - fc0;
+  g->d_flops_split = ctx->flops_split - fs0;
+  ctx->updates = u0;
+  ctx->flops_contr = fc0;
+  ctx->flops_split = fs0;
+  if (!ok) {
+    cudaGetLastError();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  return ok;
+}
+
+}  // namespace
+
 extern "C" xtrg_status xtrg_double(xtrg_ctx* ctx) {
   if (!ctx) return XTRG_EINVAL;
   if (!ctx->have_rho) return fail(ctx, XTRG_EINVAL, "xtrg_double before xtrg_init");
   ctx->use_mixed = mixed_for_beta(ctx, ctx->beta);
-  if (ctx->rho_canonical) {
-    // rho from init/double is already right-canonical: right-canonicalising
-    // it again changes only the gauge, so the guess is a plain copy
-    ctx->C.dims = ctx->rho.dims;
-    for (int i = 0; i < ctx->L; ++i)
-      CK(cudaMemcpyAsync(ctx->C.site[i], ctx->rho.site[i], sizeof(double) * site_elems(ctx->rho, i),
-                         cudaMemcpyDeviceToDevice, ctx->st));
+  if (ctx->use_mixed && ctx->rho_canonical) {
+    // tensor-core doubling.  Once the bonds are saturated (rho's bonds as at
+    // the previous tensor-core doubling, so every launch has the same shape
+    // as then), the device work is captured as a CUDA graph per buffer
+    // parity and replayed; the host reads the product's results once.
+    xtrg_ctx::DoublingGraph* hit = nullptr;
+    const bool graphable = !ctx->graphs_off && !ctx->profiling && !debug_on() &&
+                           !graphs_disabled_by_env();
+    if (graphable) {
+      for (auto& g : ctx->graphs)
+        if (g.rho0 == ctx->rho.site[0] && g.dims == ctx->rho.dims) hit = &g;
+      if (!hit && ctx->rho.dims == ctx->prev_mixed_dims) {
+        xtrg_ctx::DoublingGraph g;
+        g.rho0 = ctx->rho.site[0];
+        g.dims = ctx->rho.dims;
+        if (capture_doubling(ctx, &g)) {
+          // a stale graph of this parity (other bonds) is replaced
+          for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+            if (it->rho0 == g.rho0) {
+              cudaGraphExecDestroy(it->exec);
+              it = ctx->graphs.erase(it);
+            } else {
+              ++it;
+            }
+          }
+          ctx->graphs.push_back(g);
+          hit = &ctx->graphs.back();
+          ctx->graph_captures++;
+        } else {
+          ctx->graphs_off = true;
+        }
+      }
+    }
+    ctx->prev_mixed_dims = ctx->rho.dims;
+    if (hit) {
+      CK(cudaGraphLaunch(hit->exec, ctx->st));
+      ctx->C.dims = hit->out_dims;
+      ctx->updates += hit->d_updates;
+      ctx->flops_contr += hit->d_flops_contr;
+      ctx->flops_split += hit->d_flops_split;
+      __atomic_add_fetch(&g_xtrg_launches, hit->d_launches, __ATOMIC_RELAXED);
+      __atomic_add_fetch(&g_orth_cluster_calls, hit->d_cluster, __ATOMIC_RELAXED);
+      ctx->graph_replays++;
+    } else {
+      TRY(mixed_doubling_body(ctx));
+    }
+    TRY(finish_mixed(ctx));
+    TRY(resolve_events(ctx));
   } else {
-    TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, ctx->C));
-  }
-  if (ctx->use_mixed) {
-    TRY(mixed_prepare(ctx));
-    TRY(compress_mixed(ctx, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
-  } else {
-    TRY(compress(ctx, ctx->rho, ctx->rho, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+    if (ctx->rho_canonical) {
+      // rho from init/double is already right-canonical: right-canonicalising
+      // it again changes only the gauge, so the guess is a plain copy
+      ctx->C.dims = ctx->rho.dims;
+      for (int i = 0; i < ctx->L; ++i)
+        CK(cudaMemcpyAsync(ctx->C.site[i], ctx->rho.site[i],
+                           sizeof(double) * site_elems(ctx->rho, i), cudaMemcpyDeviceToDevice,
+                           ctx->st));
+    } else {
+      TRY(canonicalize(ctx, ctx->rho.dims, ctx->rho.site, ctx->C));
+    }
+    if (ctx->use_mixed) {
+      TRY(mixed_prepare(ctx));
+      TRY(compress_mixed(ctx, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+      TRY(finish_mixed(ctx));
+      TRY(resolve_events(ctx));
+    } else {
+      TRY(compress(ctx, ctx->rho, ctx->rho, ctx->C, ctx->cfg.dstar, ctx->cfg.sweeps));
+    }
+    TRY(normalize_device(ctx, ctx->C));
   }
   double lns = 0.0;
-  TRY(normalize(ctx, ctx->C, &lns));
+  TRY(normalize_finish(ctx, &lns));
   std::swap(ctx->rho, ctx->C);
   ctx->lnc = 2.0 * ctx->lnc + lns;
   ctx->beta *= 2.0;
@@ -1360,11 +1545,14 @@ extern "C" xtrg_status xtrg_observables(xtrg_ctx* ctx, xtrg_obs* o) {
   // the stored rho is normalised, ||rho||_F = 1, so Z(2 beta) = e^{2 ln c}
   o->lnZ2 = 2.0 * ctx->lnc;
   o->trunc_err = ctx->last_trunc;
-  double fro = 0.0, trr = 0.0;
-  TRY(herm_transfers(ctx, &fro, &trr));
-  if (!(fro > 0.0) || !std::isfinite(fro) || !std::isfinite(trr))
-    return fail(ctx, XTRG_ENUMERIC, "||rho||_F^2 = %g, Tr(rho rho) = %g", fro, trr);
-  o->herm_defect = std::sqrt(std::fmax(0.0, 2.0 - 2.0 * trr / fro));
+  o->herm_defect = NAN;
+  if (ctx->herm_check) {
+    double fro = 0.0, trr = 0.0;
+    TRY(herm_transfers(ctx, &fro, &trr));
+    if (!(fro > 0.0) || !std::isfinite(fro) || !std::isfinite(trr))
+      return fail(ctx, XTRG_ENUMERIC, "||rho||_F^2 = %g, Tr(rho rho) = %g", fro, trr);
+    o->herm_defect = std::sqrt(std::fmax(0.0, 2.0 - 2.0 * trr / fro));
+  }
   int mx = 1;
   for (int d : ctx->rho.dims) mx = d > mx ? d : mx;
   o->max_bond = mx;
@@ -1593,13 +1781,19 @@ extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
   o->split_ms = ctx->split_ms;
   o->orth_cluster_calls = (long long)__atomic_load_n(&g_orth_cluster_calls, __ATOMIC_RELAXED);
   o->orth_fallbacks = 0;
+  o->orth_full_second_pass = 0;
+  o->graph_captures = ctx->graph_captures;
+  o->graph_replays = ctx->graph_replays;
+  o->orth_deflated_columns = 0;
   if (ctx->mixed_ready && ctx->m.sb.chol_flag) {
-    int h[2] = {0, 0};
+    int h[5] = {0, 0, 0, 0, 0};
     if (cudaMemcpyAsync(h, ctx->m.sb.chol_flag, sizeof h, cudaMemcpyDeviceToHost, ctx->st) !=
             cudaSuccess ||
         cudaStreamSynchronize(ctx->st) != cudaSuccess)
       return XTRG_ECUDA;
     o->orth_fallbacks = h[1];
+    o->orth_full_second_pass = h[3];
+    o->orth_deflated_columns = h[4];
   }
   o->fp64_update_ms = ctx->tag_ms[TAG_UPDATE64];
   o->fp64_updates_timed = ctx->tag_n[TAG_UPDATE64];
@@ -1610,6 +1804,22 @@ extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
 extern "C" xtrg_status xtrg_set_profiling(xtrg_ctx* ctx, int on) {
   if (!ctx) return XTRG_EINVAL;
   ctx->profiling = on != 0;
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_set_herm_check(xtrg_ctx* ctx, int on) {
+  if (!ctx) return XTRG_EINVAL;
+  ctx->herm_check = on != 0;
+  return XTRG_OK;
+}
+
+extern "C" xtrg_status xtrg_set_graphs(xtrg_ctx* ctx, int on) {
+  if (!ctx) return XTRG_EINVAL;
+  ctx->graphs_off = on == 0;
+  if (!on) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+  }
   return XTRG_OK;
 }
 
@@ -1729,5 +1939,7 @@ extern "C" void xtrg_destroy(xtrg_ctx* ctx) {
                 ctx->tag_ms[t] > 0 ? ctx->tag_flops[t] / ctx->tag_ms[t] / 1e9 : 0.0);
   }
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   delete ctx;
 }

@@ -131,6 +131,16 @@ class XTRG:
     def set_profiling(self, on=True):
         _lib.xtrg_set_profiling(self.ctx, on)
 
+    def set_herm_check(self, on=True):
+        """Compute (default) or skip the Hermiticity diagnostic in
+        observables() (herm_defect is NaN when skipped)."""
+        _lib.xtrg_set_herm_check(self.ctx, on)
+
+    def set_graphs(self, on=True):
+        """Allow (default) or forbid replaying saturated tensor-core doublings
+        from captured CUDA graphs."""
+        _lib.xtrg_set_graphs(self.ctx, on)
+
     def close(self):
         if getattr(self, "ctx", None):
             _lib.xtrg_destroy(self.ctx)

@@ -1,8 +1,7 @@
 // tcgen05 / TMA GEMM kernel (see tc_gemm.cuh).
 //
 // CTA tile 128 x 128 (M x N), K-block of 64 BF16 (one 128-byte swizzle row;
-// 2 stages at 6 planes) or 32 BF16 (64-byte swizzle; 4 stages at 6 planes);
-// persistent CTAs (one per SM).  Warp 0: TMA producer (one elected thread);
+// 2 stages at 6 planes); persistent CTAs (one per SM).  Warp 0: TMA producer (one elected thread);
 // warp 1: MMA issuer (one elected thread, 4 x UMMA_K=16 per K-block and
 // product); warp 2: tensor-memory allocation; warps 4-7: epilogue
 // (tcgen05.ld 32x32b, lane quarter = warp % 4).
@@ -297,7 +296,14 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // K-blocks and the corr accumulator per tile, so the MMAs of the next chunk
 // (and of the next tile) run while the epilogue drains and stores; the
 // operand stage ring continues across tiles.
-template <int BK>
+//
+// The operand layout of B (BMN: MN-major) and the number of plane products
+// (NPROD: 1, 3 or 6) are template parameters: the MMA issuer is one thread
+// that must issue a 128x128x16 MMA about every 70 cycles, so its loop holds
+// no branches on them and its descriptors are the stage's two base
+// descriptors plus compile-time offsets (measured: the runtime-selected
+// descriptors alone cost 16 % of the kernel's time).
+template <int BK, int BMN, int NPROD>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const KParams p) {
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int tiles_n = (p.N + BN - 1) / BN, tiles_m = (p.M + BM - 1) / BM;
   const int tiles = tiles_n * tiles_m * p.batch * p.splitk;
   const int CK = p.chunk_kb;
-  const bool has_corr = p.nprod > 1;
+  constexpr bool has_corr = NPROD > 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -352,6 +358,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     long long g = 0;   // k-blocks issued by this CTA
+    int s = 0;         // stage of k-block g, and the parity of its round
+    uint32_t ph = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
       int mt, nt, z;
@@ -361,29 +369,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int kb_end = min(kb_begin + p.kb_per, p.kb_total);
       const int ba = p.a_batched ? bidx : 0, bb = p.b_batched ? bidx : 0;
       for (int kb = kb_begin; kb < kb_end && ok; ++kb, ++g) {
-        const int s = (int)(g % S);
-        if (g >= S) ok = mbar_wait(&empty[s], (uint32_t)(((g / S) - 1) & 1), p.err);
+        if (g >= S) ok = mbar_wait(&empty[s], ph ^ 1u, p.err);
         if (!ok) break;
         uint8_t* st = smem + s * stage_bytes;
         mbar_expect_tx(&full[s], stage_bytes);
         const int k0 = kb * BK;
-        for (int q = 0; q < p.pa_planes; ++q) {
-          uint8_t* dst = st + q * G::TILE;
-          if (p.a_mn) {
-            for (int a = 0; a < G::ATOMS; ++a)
-              tma_load_4d(dst + a * G::ATOM, &mapA, &full[s], mt * BM + a * BK, k0, ba, q);
-          } else {
-            tma_load_4d(dst, &mapA, &full[s], k0, mt * BM, ba, q);
-          }
-        }
+        for (int q = 0; q < p.pa_planes; ++q)
+          tma_load_4d(st + q * G::TILE, &mapA, &full[s], k0, mt * BM, ba, q);
         for (int q = 0; q < p.pb_planes; ++q) {
           uint8_t* dst = st + (p.pa_planes + q) * G::TILE;
-          if (p.b_mn) {
+          if (BMN) {
+#pragma unroll
             for (int a = 0; a < G::ATOMS; ++a)
               tma_load_4d(dst + a * G::ATOM, &mapB, &full[s], nt * BN + a * BK, k0, bb, q);
           } else {
             tma_load_4d(dst, &mapB, &full[s], k0, nt * BN, bb, q);
           }
+        }
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
         }
       }
     }
@@ -392,8 +397,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), p.err);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    const uint32_t idesc = idesc_bf16_128x128(p.a_mn, p.b_mn);
-    long long g = 0;   // k-blocks consumed (stage ring position)
+    // plane products: (0,0) is the main one, then (0,1) (1,0) (0,2) (1,1) (2,0)
+    constexpr int PA[6] = {0, 0, 1, 0, 1, 2}, PB[6] = {0, 1, 0, 2, 1, 0};
+    constexpr uint32_t PLANE = G::TILE >> 4;                 // descriptor units per plane
+    constexpr uint32_t KSTEP_A = 2;                          // 16 BF16 = 32 B along K
+    constexpr uint32_t KSTEP_B = BMN ? (16 * G::SW) >> 4 : 2;   // MN-major: 16 K-rows
+    const uint32_t idesc = idesc_bf16_128x128(0, BMN);
+    const uint32_t boff = (uint32_t)(p.pa_planes * G::TILE);
+    int s = 0;         // stage of the current k-block, and the parity of its round
+    uint32_t ph = 0;
     long long h = 0;   // main chunks issued
     int j = 0;         // tiles of this CTA
     bool ok = true;
@@ -406,31 +418,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (has_corr && j >= 2) ok = mbar_wait(&corr_empty[cb], (uint32_t)(((j >> 1) - 1) & 1), p.err);
       if (!ok) break;
       const uint32_t ccol = tmem + (uint32_t)(CORR_COL + cb * BN);
-      for (int kb = kb_begin; kb < kb_end && ok; ++kb, ++g) {
-        const int ci = (kb - kb_begin) % CK;   // position inside the main chunk
+      int ci = 0;   // position inside the main chunk
+      for (int kb = kb_begin; kb < kb_end && ok; ++kb) {
         const int mb = (int)(h & 1);
         if (ci == 0 && h >= 2) ok = mbar_wait(&main_empty[mb], (uint32_t)(((h >> 1) - 1) & 1), p.err);
         if (!ok) break;
-        const int s = (int)(g % S);
-        ok = mbar_wait(&full[s], (uint32_t)((g / S) & 1), p.err);
+        ok = mbar_wait(&full[s], ph, p.err);
         if (!ok) break;
         fence_after();
         const uint32_t base = smem_u32(smem + s * stage_bytes);
+        const uint64_t dA = smem_desc<BK>(base);
+        const uint64_t dB = BMN ? smem_desc_mn<BK>(base + boff) : smem_desc<BK>(base + boff);
         const uint32_t mcol = tmem + (uint32_t)(mb * BN);
-        for (int pr = 0; pr < p.nprod; ++pr) {
-          const uint32_t a_addr = base + p.prod_a[pr] * G::TILE;
-          const uint32_t b_addr = base + (p.pa_planes + p.prod_b[pr]) * G::TILE;
-          const uint32_t dcol = pr == 0 ? mcol : ccol;
+        const bool main_acc = ci > 0, corr_acc = kb > kb_begin;
+#pragma unroll
+        for (int pr = 0; pr < NPROD; ++pr) {
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            // K-major: advance 16 BF16 = 32 B along K inside the swizzled
-            // row; MN-major: advance 16 K-rows of SW bytes
-            uint64_t da = p.a_mn ? smem_desc_mn<BK>(a_addr + kk * 16 * G::SW)
-                                 : smem_desc<BK>(a_addr) + (uint64_t)(kk * 2);
-            uint64_t db = p.b_mn ? smem_desc_mn<BK>(b_addr + kk * 16 * G::SW)
-                                 : smem_desc<BK>(b_addr) + (uint64_t)(kk * 2);
-            const bool acc = pr == 0 ? (ci > 0 || kk > 0) : (kb > kb_begin || pr > 1 || kk > 0);
-            mma_bf16(dcol, da, db, idesc, acc ? 1u : 0u);
+            const uint64_t da = dA + (uint64_t)(PA[pr] * PLANE + kk * KSTEP_A);
+            const uint64_t db = dB + (uint64_t)(PB[pr] * PLANE + kk * KSTEP_B);
+            const bool acc = kk > 0 || (pr == 0 ? main_acc : (pr > 1 || corr_acc));
+            mma_bf16(pr == 0 ? mcol : ccol, da, db, idesc, acc ? 1u : 0u);
           }
           if (pr == 0 && (ci == CK - 1 || kb == kb_end - 1)) {
             // the chunk's leading products are issued: the epilogue may take it
@@ -439,6 +447,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         mma_commit(&empty[s]);
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
+        if (++ci == CK) ci = 0;
       }
       // an empty tile (split beyond K) commits nothing it would have to wait for
       if (ok && has_corr) mma_commit(&corr_full[cb]);
@@ -602,16 +615,21 @@ struct LaunchSetup {
 };
 PerDevice<LaunchSetup> g_launch_setup;
 
+template <int BMN, int NPROD>
+cudaError_t opt_in() {
+  return cudaFuncSetAttribute(tc_gemm_kernel<64, BMN, NPROD>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 cudaError_t launch_setup(int* sms) {
   LaunchSetup s{cudaSuccess, 0};
   cudaError_t e = g_launch_setup.get(
       [](int dev) {
         LaunchSetup r{cudaSuccess, 0};
-        r.err = cudaFuncSetAttribute(tc_gemm_kernel<64>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (r.err == cudaSuccess)
-          r.err = cudaFuncSetAttribute(tc_gemm_kernel<32>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        const cudaError_t o[6] = {opt_in<0, 1>(), opt_in<0, 3>(), opt_in<0, 6>(),
+                                  opt_in<1, 1>(), opt_in<1, 3>(), opt_in<1, 6>()};
+        for (cudaError_t x : o)
+          if (r.err == cudaSuccess) r.err = x;
         if (r.err == cudaSuccess)
           r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
         return r;
@@ -635,14 +653,9 @@ int chunk_terms() {
   return v;
 }
 
-// K-block width: XTRG_TC_BK = 32 or 64 if set, else 64
-int k_block() {
-  static const int v = []() {
-    const char* e = getenv("XTRG_TC_BK");
-    return (e && atoi(e) == 32) ? 32 : 64;
-  }();
-  return v;
-}
+// K-block width: 64 BF16 (one 128-byte swizzle row).  A 32-wide K-block
+// (64-byte swizzle, twice the stages) computed the same and was slower.
+constexpr int K_BLOCK = 64;
 
 // 4-D map with BK-wide boxes (BK = 64: 128-byte swizzle, 32: 64-byte),
 // out-of-range elements read as zero.
@@ -680,7 +693,9 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   if ((A.batches != 1 && A.batches != batch) || (B.batches != 1 && B.batches != batch))
     return cudaErrorInvalidValue;
   if (splitk > 1 && out.mode != TC_OUT_PARTIAL) return cudaErrorInvalidValue;
-  const int BK = k_block();
+  // A is staged K-major; B K-major or MN-major
+  if (A.mn_major) return cudaErrorInvalidValue;
+  const int BK = K_BLOCK;
   KParams p;
   p.M = M; p.N = N; p.K = K; p.batch = batch; p.splitk = splitk;
   p.kb_total = (K + BK - 1) / BK;
@@ -721,9 +736,14 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, int M, int N, int K,
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(tiles < sms ? tiles : sms));
   note_launch();
-  if (BK == 32)
-    tc_gemm_kernel<32><<<grid, NTHREADS, smem, st>>>(ma, mb, p);
-  else
-    tc_gemm_kernel<64><<<grid, NTHREADS, smem, st>>>(ma, mb, p);
+  const int sel = (B.mn_major ? 3 : 0) + (nprod == 1 ? 0 : nprod == 3 ? 1 : 2);
+  switch (sel) {
+    case 0: tc_gemm_kernel<64, 0, 1><<<grid, NTHREADS, smem, st>>>(ma, mb, p); break;
+    case 1: tc_gemm_kernel<64, 0, 3><<<grid, NTHREADS, smem, st>>>(ma, mb, p); break;
+    case 2: tc_gemm_kernel<64, 0, 6><<<grid, NTHREADS, smem, st>>>(ma, mb, p); break;
+    case 3: tc_gemm_kernel<64, 1, 1><<<grid, NTHREADS, smem, st>>>(ma, mb, p); break;
+    case 4: tc_gemm_kernel<64, 1, 3><<<grid, NTHREADS, smem, st>>>(ma, mb, p); break;
+    default: tc_gemm_kernel<64, 1, 6><<<grid, NTHREADS, smem, st>>>(ma, mb, p); break;
+  }
   return cudaGetLastError();
 }

@@ -416,6 +416,8 @@ def run_native(args):
            "orth_cluster_calls": s1["orth_cluster_calls"] - s0["orth_cluster_calls"],
            "orth_fallbacks": s1["orth_fallbacks"] - s0["orth_fallbacks"],
            "orth_full_second_pass": s1["orth_full_second_pass"] - s0["orth_full_second_pass"],
+           "orth_deflated_columns": s1["orth_deflated_columns"] - s0["orth_deflated_columns"],
+           "graph_replays_timed": s1["graph_replays"] - s0["graph_replays"],
            "fp64_arm": fp64,
            "observables_last": {k: rows[-1][k] for k in ("beta", "lnZ", "f", "u", "max_bond")},
            "herm_defect_last": {"beta": herm_last["beta"], "herm_defect": herm_last["herm_defect"],

@@ -610,6 +610,18 @@ OrthSetup orth_setup() {
   return s;
 }
 
+// C[m][n] (row stride ldc) = sum over s of part[s][m][n]
+__global__ void sum_partials_kernel(const float* __restrict__ part, int splitk, int M, int N,
+                                    float* __restrict__ C, long long ldc) {
+  const long long MN = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN;
+       e += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int s = 0; s < splitk; ++s) acc += part[s * MN + e];
+    C[(e / N) * ldc + e % N] = acc;
+  }
+}
+
 #define RET(x)                                 \
   do {                                         \
     cudaError_t _e = (x);                      \
@@ -644,12 +656,32 @@ cudaError_t tc_product(const View& a, const View& b, int M, int N, int K, float*
   else RET(to_planes_f32(b.f, b.rv, b.kv, 0, N, K, 1, buf.pb, ld, 0, 3, buf.psb, st));
   TcOutput o;
   memset(&o, 0, sizeof o);
-  o.mode = TC_OUT_F32;
-  o.f32 = C;
-  o.cm = idx_plain(ldc);
-  o.cn = idx_plain(1);
   o.alpha = 1.0;
-  return tc_gemm(A, B, M, N, K, 1, 6, 1, o, buf.err, st);
+  // products with few output tiles (the k x k Grams, the k-wide factors)
+  // split K so that about one wave of CTAs runs, partials summed after
+  const int kb = (K + 63) / 64, tiles = ((M + 127) / 128) * ((N + 127) / 128);
+  int splitk = 1;
+  if (buf.part && tiles < 76) {
+    int sk = 152 / tiles;
+    sk = sk < kb ? sk : kb;
+    sk = sk < 32 ? sk : 32;
+    const int per = (kb + sk - 1) / sk;
+    sk = (kb + per - 1) / per;
+    if ((size_t)sk * M * N <= buf.part_floats) splitk = sk;
+  }
+  if (splitk == 1) {
+    o.mode = TC_OUT_F32;
+    o.f32 = C;
+    o.cm = idx_plain(ldc);
+    o.cn = idx_plain(1);
+    return tc_gemm(A, B, M, N, K, 1, 6, 1, o, buf.err, st);
+  }
+  o.mode = TC_OUT_PARTIAL;
+  o.f32 = buf.part;
+  RET(tc_gemm(A, B, M, N, K, 1, 6, splitk, o, buf.err, st));
+  note_launch();
+  sum_partials_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(buf.part, splitk, M, N, C, ldc);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -670,7 +702,7 @@ cudaError_t tc_product(const View& a, const View& b, int M, int N, int K, float*
 // untouched Y instead (they return at once when *flag is 0).  A column
 // whose norm is zero is dead: its output column is zero, as in the block
 // Gram-Schmidt kernels.
-constexpr int CQ_NT = 512;        // threads of the factor kernel
+constexpr int CQ_NT = 384;        // threads of the factor kernel (12 warps: up to 170 registers)
 constexpr int CQ_SOLVE_NT = 256;  // threads of the solve kernel (8 warps, one row each)
 
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
@@ -710,6 +742,7 @@ __global__ void __launch_bounds__(CQ_NT, 1)
   float* li = d + MAX_K;                            // 1 / L_jj
   __shared__ float red[32];
   __shared__ int bad, ndefl;
+  __shared__ __align__(16) float colb[32];   // column of the diagonal-block step
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   float gm = 0.f;
   for (int j = tid; j < k; j += CQ_NT) {
@@ -735,13 +768,25 @@ __global__ void __launch_bounds__(CQ_NT, 1)
     d[j] = (g > 1e-30f * gmax && g < 3.0e38f) ? 1.f / sqrtf(g) : 0.f;
   }
   __syncthreads();
-  // packed load, row by row (one warp per row, coalesced reads of G)
+  // packed load, row by row (one warp per row, coalesced reads of G); the
+  // row's eight loads are issued before any is used, so a warp waits on the
+  // memory latency once per row rather than once per 32 columns
   for (int i = warp; i < k; i += CQ_NT / 32) {
     const float di = d[i];
-    for (int j = lane; j <= i; j += 32) {
-      const float v = G[(long long)i * k + j] * di * d[j];
-      A[pk(i, j)] = (v == v) ? v : 0.f;
-      if (v != v) bad = 1;
+    float g[MAX_K / 32];
+#pragma unroll
+    for (int t = 0; t < MAX_K / 32; ++t) {
+      const int j = lane + 32 * t;
+      g[t] = j <= i ? G[(long long)i * k + j] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < MAX_K / 32; ++t) {
+      const int j = lane + 32 * t;
+      if (j <= i) {
+        const float v = g[t] * di * d[j];
+        A[pk(i, j)] = (v == v) ? v : 0.f;
+        if (v != v) bad = 1;
+      }
     }
   }
   __syncthreads();
@@ -752,35 +797,50 @@ __global__ void __launch_bounds__(CQ_NT, 1)
       float r[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) r[c] = (lane < pw && c <= lane) ? A[pk(p0 + lane, p0 + c)] : 0.f;
+      // dead columns of the block (zero scaling) as one bit per lane; pivots
+      // that break down, collected the same way (the pivot is warp-uniform)
+      const unsigned deadm = __ballot_sync(0xffffffffu, lane < pw && d[p0 + lane] == 0.f);
+      unsigned brokem = 0;
+      float myinv = 0.f;
+      // Per step, the pivot comes by one shuffle; the new column L_.,j goes
+      // through shared memory and is read back as float4 broadcasts (a
+      // shuffle per trailing column made each step several hundred cycles).
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         if (j < pw) {
           const float piv = __shfl_sync(0xffffffffu, r[j], j);
-          const bool dead = d[p0 + j] == 0.f;
+          const bool dead = (deadm >> j) & 1u;
           const bool broke = !dead && !(piv > tau);
-          // 1 / L_jj by the approximate reciprocal square root (a few ulp;
-          // the second pass absorbs it) to keep the pivot chain short
           const float rs = rsqrtf(piv);
-          const float ljj = (dead || broke) ? 1.f : piv * rs;
-          const float inv = (dead || broke) ? 0.f : rs;
-          if (lane == j) {
-            r[j] = ljj;
-            li[p0 + j] = inv;
-            if (broke) {
-              if (deflate) ++ndefl;
-              else bad = 1;
-            }
-          }
-          if (lane > j) r[j] *= inv;
-          // trailing part of the block: r[c] -= L_lane,j L_c,j for j < c <= lane
+          const bool good = !(dead || broke);
+          const float ljj = good ? piv * rs : 1.f;
+          const float inv = good ? rs : 0.f;
+          if (broke) brokem |= 1u << j;
+          if (lane == j) myinv = inv;
+          const float lj = r[j] * inv;   // L_lane,j (lane > j)
+          r[j] = lane == j ? ljj : (lane > j ? lj : r[j]);
+          if (j < 31) {
+            colb[lane] = lj;
+            __syncwarp();
+            // trailing part of the block: r[c] -= L_lane,j L_c,j for j < c <= lane
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            if (c > j) {
-              const float lcj = __shfl_sync(0xffffffffu, r[j], c);
-              if (lane >= c) r[c] -= r[j] * lcj;
+            for (int c4 = (j + 1) / 4; c4 < 8; ++c4) {
+              const float4 x4 = *reinterpret_cast<const float4*>(colb + 4 * c4);
+              const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int c = 4 * c4 + u;
+                if (c > j) r[c] = lane >= c ? fmaf(-lj, xs[u], r[c]) : r[c];
+              }
             }
+            __syncwarp();
           }
         }
+      }
+      if (lane < pw) li[p0 + lane] = myinv;
+      if (lane == 0 && brokem) {
+        if (deflate) ndefl += __popc(brokem);
+        else bad = 1;
       }
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
@@ -885,7 +945,12 @@ __global__ void __launch_bounds__(CQ_SOLVE_NT)
   if (*flag || (run_if && *run_if == 0)) return;
   extern __shared__ __align__(16) float Ls[];
   const int np = k * (k + 1) / 2;
-  for (int e = threadIdx.x; e < np; e += CQ_SOLVE_NT) Ls[e] = Lp[e];
+  // the packed factor (16-byte aligned in global memory), 16 bytes per load
+  const int n4 = np / 4;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < n4; e += CQ_SOLVE_NT)
+    reinterpret_cast<float4*>(Ls)[e] = reinterpret_cast<const float4*>(Lp)[e];
+  for (int e = 4 * n4 + threadIdx.x; e < np; e += CQ_SOLVE_NT) Ls[e] = Lp[e];
   __syncthreads();
   const int lane = threadIdx.x % 32;
   const int WPB = CQ_SOLVE_NT / 32;

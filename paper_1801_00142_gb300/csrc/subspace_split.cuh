@@ -34,6 +34,8 @@ struct SubspaceBuffers {
   int* chol_flag;         // [0] breakdown flag of the current call, [1] count of breakdowns,
                           // [2] full second pass flag, [3] its count, [4] deflated columns
   int orth_block;         // column-block width of the orthonormalisation (32..SUBSPACE_BLOCK_K)
+  float* part;            // FP32 split-K partials of the small tensor-core products (may be
+  size_t part_floats;     // shared with other split-K users: free during a split)
 };
 
 // Widest column block the one-block orthonormalisation kernels take, and the

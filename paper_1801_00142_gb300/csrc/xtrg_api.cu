@@ -1156,6 +1156,9 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
       ctx->m.sb.chol_li = (float*)carve(ctx, SUBSPACE_BLOCK_K * 4);
       ctx->m.sb.chol_flag = (int*)carve(ctx, 32);
       ctx->m.sb.orth_block = cfg->orth_block ? cfg->orth_block : SUBSPACE_BLOCK_K;
+      // C_E's split-K partials are consumed before the split starts
+      ctx->m.sb.part = ctx->m.part;
+      ctx->m.sb.part_floats = p.m_part;
       ok = ok && ctx->m.sb.ce_rm && ctx->m.sb.ce_tr && ctx->m.sb.ce_ss && ctx->m.sb.chol_L &&
            ctx->m.sb.chol_d && ctx->m.sb.chol_li && ctx->m.sb.chol_flag;
       ok = ok && ctx->m.sb.dscal && ctx->m.sb.pa && ctx->m.sb.pb;

@@ -468,7 +468,22 @@ def fp64_arm(XTRG, host_state, dev):
     n_upd = c1["fp64_updates_timed"] - c0["fp64_updates_timed"]
     upd_ms = (c1["fp64_update_ms"] - c0["fp64_update_ms"]) / max(1, n_upd)
     extra = (W.sweeps - 1) * 2 * (W.L - 1)
+    # FP64 denominator: cuBLAS DGEMM (torch.matmul, 4096^3) on this GPU; the
+    # FP64 path's contractions per update are 88 D*^4 flops (both halves)
+    x = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        torch.matmul(x, x)
+    a.record()
+    for _ in range(5):
+        torch.matmul(x, x)
+    b.record()
+    torch.cuda.synchronize(dev)
+    dgemm_tflops = 5 * 2 * 4096.0 ** 3 / (a.elapsed_time(b) / 1e3) / 1e12
+    upd_tflops = 88.0 * W.dstar ** 4 / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
     return {"ms_per_step": t1 + extra * upd_ms, "measured_ms_1_sweep": t1,
+            "dgemm_tflops_measured": dgemm_tflops,
+            "update_contraction_tflops": upd_tflops,
+            "update_frac_of_dgemm": upd_tflops / dgemm_tflops if upd_tflops else None,
             "updates_timed": n_upd, "ms_per_update": upd_ms,
             "env_pass_ms": c1["fp64_env_pass_ms"] - c0["fp64_env_pass_ms"],
             "beta": beta, "mixed_vs_fp64_abs_df": abs(om["f"] - o64["f"]),

@@ -232,6 +232,8 @@ typedef struct {
                                 dependent on the columns before them (this context) */
   long long graph_captures;  /* tensor-core doublings captured as a CUDA graph (this context) */
   long long graph_replays;   /* tensor-core doublings run by replaying a captured graph */
+  long long split_shapes_tuned; /* C_E shapes whose split-K the autotuner has chosen by timing
+                                the candidates (all contexts of the process share the choice) */
 } xtrg_stats;
 
 /* Counters since creation (kernel_launches: since the library was loaded).

@@ -63,7 +63,7 @@ class xtrg_stats(C.Structure):
                 ("fp64_env_pass_ms", C.c_double), ("orth_fallbacks", C.c_longlong),
                 ("orth_full_second_pass", C.c_longlong), ("orth_deflated_columns", C.c_longlong),
                 ("graph_captures", C.c_longlong),
-                ("graph_replays", C.c_longlong)]
+                ("graph_replays", C.c_longlong), ("split_shapes_tuned", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -733,6 +733,7 @@ __global__ void __launch_bounds__(CQ_NT, 1)
                   float* __restrict__ Lout, float* __restrict__ dout, float* __restrict__ linv_out,
                   int* flag, const int* run_if) {
   if (run_if && (*run_if == 0 || *flag)) return;
+  if (run_if && threadIdx.x == 0) atomicAdd(const_cast<int*>(run_if) + 1, 1);
   extern __shared__ __align__(16) float cq[];
   const int np = k * (k + 1) / 2;
   float* A = cq;                                    // packed lower triangle
@@ -1098,8 +1099,8 @@ __global__ void subtract_block_kernel(float* __restrict__ Yb, long long ldy,
 // Writes B = I - Phi(E) (k x k row-major: U2 = U1 B^T is one tensor-core
 // product); dead columns (G2_jj < 1/2, zero columns of U1) keep B's row e_j
 // and get zeros elsewhere.  If a live |E_ij| exceeds emax (or is not
-// finite), sets *need_full (and counts it in need_full[1]): the full second
-// pass runs instead.
+// finite), sets *need_full: the full second pass runs instead (and counts
+// itself in need_full[1]).
 __global__ void cholqr_linear_kernel(const float* __restrict__ G, int k, float emax,
                                      float* __restrict__ B, int* need_full) {
   bool big = false;
@@ -1119,10 +1120,7 @@ __global__ void cholqr_linear_kernel(const float* __restrict__ G, int k, float e
     }
     B[e] = v;
   }
-  if (__syncthreads_or(big) && threadIdx.x == 0) {
-    atomicExch(need_full, 1);
-    atomicAdd(need_full + 1, 1);
-  }
+  if (__syncthreads_or(big) && threadIdx.x == 0) atomicExch(need_full, 1);
 }
 
 // dst[r][c] = src[r][c] (rows x k, contiguous) if *flag != 0

@@ -26,6 +26,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -210,6 +212,7 @@ struct xtrg_ctx {
   bool graphs_off = false;           // disabled (XTRG_NO_GRAPHS=1) or a capture failed
   bool herm_check = true;            // xtrg_observables computes herm_defect
   long long graph_replays = 0, graph_captures = 0;
+  bool tune_splits = true;   // autotune C_E's split-K (see mixed_ce)
   std::string err;
 };
 
@@ -775,6 +778,21 @@ xtrg_status mixed_env(xtrg_ctx* ctx, const double* Csite, int kout, int kin, boo
 }
 
 // C_E = Lp Rp^T (FP32 accumulation, split-K partials summed in FP64)
+// split-K of C_E chosen by the autotuner, per device, plane count and shape
+struct SplitKey {
+  int dev, planes, m, n;
+  long long K;
+  bool operator<(const SplitKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (planes != o.planes) return planes < o.planes;
+    if (m != o.m) return m < o.m;
+    if (n != o.n) return n < o.n;
+    return K < o.K;
+  }
+};
+std::map<SplitKey, int> g_split_tuned;
+std::mutex g_split_mu;
+
 xtrg_status mixed_ce(xtrg_ctx* ctx, const __nv_bfloat16* Lp, const __nv_bfloat16* Rp, int m, int n,
                      int a2) {
   const int P = ctx->m.P;
@@ -808,6 +826,51 @@ xtrg_status mixed_ce(xtrg_ctx* ctx, const __nv_bfloat16* Lp, const __nv_bfloat16
   TcOutput o;
   memset(&o, 0, sizeof o);
   o.mode = TC_OUT_PARTIAL; o.f32 = ctx->m.part; o.alpha = 1.0;
+  // autotuner: the first time a shape is met (outside a graph capture), the
+  // heuristic's split and its neighbours are each timed by CUDA events (two
+  // launches, the second timed) and the fastest is kept for the shape.  The
+  // choice is shared by every context of the process (under a lock, so that
+  // concurrent contexts of a batch agree), which keeps the results of equal
+  // runs in one process identical.
+  int dev = 0;
+  CKM(cudaGetDevice(&dev));
+  const SplitKey key{dev, P, m, n, K};
+  std::unique_lock<std::mutex> lock(g_split_mu);
+  const auto hit = g_split_tuned.find(key);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CKM(cudaStreamIsCapturing(ctx->st, &cap));
+  if (hit != g_split_tuned.end()) {
+    splitk = hit->second;
+  } else if (ctx->tune_splits && cap == cudaStreamCaptureStatusNone && kb >= 16) {
+    const int lim = SPLITK_MAX < kb / 4 ? SPLITK_MAX : kb / 4;
+    const int cand[4] = {splitk, splitk / 2, 2 * splitk, (3 * splitk + 1) / 2};
+    cudaEvent_t e0, e1;
+    CKM(cudaEventCreate(&e0));
+    CKM(cudaEventCreate(&e1));
+    int best = splitk;
+    float best_ms = 1e30f;
+    for (int c = 0; c < 4; ++c) {
+      const int sk = cand[c];
+      if (sk < 1 || sk > lim || (c > 0 && sk == splitk)) continue;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        CKM(cudaEventRecord(e0, ctx->st));
+        CKM(tc_gemm(Al, Br, m, n, (int)K, 1, ctx->m.nprod, sk, o, ctx->m.err, ctx->st));
+        CKM(cudaEventRecord(e1, ctx->st));
+        CKM(cudaEventSynchronize(e1));
+        CKM(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = sk;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_split_tuned[key] = best;
+    splitk = best;
+  }
+  lock.unlock();
   TRY(tc(ctx, Al, Br, m, n, (int)K, 1, splitk, o));
   // FP64 C_E (exact fallback, debug scans), its planes in both orientations
   // for the subspace products and ||C_E||^2, in one pass over the partials
@@ -1787,6 +1850,10 @@ extern "C" xtrg_status xtrg_get_stats(const xtrg_ctx* ctx, xtrg_stats* o) {
   o->orth_full_second_pass = 0;
   o->graph_captures = ctx->graph_captures;
   o->graph_replays = ctx->graph_replays;
+  {
+    std::lock_guard<std::mutex> lock(g_split_mu);
+    o->split_shapes_tuned = (long long)g_split_tuned.size();
+  }
   o->orth_deflated_columns = 0;
   if (ctx->mixed_ready && ctx->m.sb.chol_flag) {
     int h[5] = {0, 0, 0, 0, 0};

@@ -50,13 +50,6 @@ __global__ void reduce_partials_kernel(const float* __restrict__ part, int split
   }
 }
 
-__device__ __forceinline__ void split3(double x, __nv_bfloat16& p0, __nv_bfloat16& p1,
-                                       __nv_bfloat16& p2) {
-  p0 = __double2bfloat16(x);
-  const double r1 = x - (double)__bfloat162float(p0);
-  p1 = __double2bfloat16(r1);
-  p2 = __double2bfloat16(r1 - (double)__bfloat162float(p1));
-}
 
 // One 32 x 32 tile of C = sum of the split-K partials: the FP64 result, its
 // three BF16 planes in both orientations (row-major [m][ldn] and transposed
@@ -69,7 +62,11 @@ __global__ void reduce_partials_planes_kernel(const float* __restrict__ part, in
                                               __nv_bfloat16* __restrict__ prm, long long ldn,
                                               __nv_bfloat16* __restrict__ ptr, long long ldm,
                                               long long ps, double* ss) {
-  __shared__ double tile[32][33];
+  // the three planes of the tile, kept for the transposed writes (FP64
+  // arithmetic is slow on this GPU: the partials are summed in FP32 with a
+  // compensation term, which keeps the sum to about FP64 accuracy for the
+  // few splits, and the planes are cut from that pair in FP32)
+  __shared__ __nv_bfloat16 tp[3][32][34];
   __shared__ double red[8];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8 threads
   const int n0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
@@ -77,21 +74,33 @@ __global__ void reduce_partials_planes_kernel(const float* __restrict__ part, in
   double acc = 0.0;
   for (int y = ty; y < 32; y += 8) {
     const int r = m0 + y, c = n0 + tx;
-    double v = 0.0;
+    float hi = 0.f, lo = 0.f;
     if (r < m && c < n) {
       const long long e = (long long)r * n + c;
-      for (int i = 0; i < splits; ++i) v += (double)part[i * mn + e];
+      for (int i = 0; i < splits; ++i) {
+        // two-sum: hi + lo = old hi + part exactly, errors gathered in lo
+        const float x = part[i * mn + e];
+        const float t = hi + x;
+        const float bp = t - hi;
+        lo += (hi - (t - bp)) + (x - bp);
+        hi = t;
+      }
+      const double v = (double)hi + (double)lo;
       out[e] = v;
       acc = fma(v, v, acc);
     }
-    tile[y][tx] = v;
+    const __nv_bfloat16 p0 = __float2bfloat16_rn(hi);
+    const float r1 = (hi - __bfloat162float(p0)) + lo;
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+    tp[0][y][tx] = p0;
+    tp[1][y][tx] = p1;
+    tp[2][y][tx] = p2;
     if (r < m && c < ldn) {
-      __nv_bfloat16 a, b, d;
-      split3(v, a, b, d);
       const long long o = (long long)r * ldn + c;
-      prm[o] = a;
-      prm[o + ps] = b;
-      prm[o + 2 * ps] = d;
+      prm[o] = p0;
+      prm[o + ps] = p1;
+      prm[o + 2 * ps] = p2;
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -105,12 +114,12 @@ __global__ void reduce_partials_planes_kernel(const float* __restrict__ part, in
   for (int y = ty; y < 32; y += 8) {
     const int r = n0 + y, c = m0 + tx;   // row r of C^T, column c
     if (r < n && c < ldm) {
-      __nv_bfloat16 a, b, d;
-      split3(c < m ? tile[tx][y] : 0.0, a, b, d);
+      const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+      const bool in = c < m;
       const long long o = (long long)r * ldm + c;
-      ptr[o] = a;
-      ptr[o + ps] = b;
-      ptr[o + 2 * ps] = d;
+      ptr[o] = in ? tp[0][tx][y] : z;
+      ptr[o + ps] = in ? tp[1][tx][y] : z;
+      ptr[o + 2 * ps] = in ? tp[2][tx][y] : z;
     }
   }
 }

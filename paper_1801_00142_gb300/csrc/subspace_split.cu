@@ -33,6 +33,7 @@
 // orthogonality (steep, rank-deficient spectra).
 #include <cooperative_groups.h>
 #include <math.h>
+#include <string.h>
 
 #include <atomic>
 
@@ -652,7 +653,11 @@ cudaError_t tc_product(const View& a, const View& b, int M, int N, int K, float*
   TcOperand B{buf.pb, 3, N, K, ld, 0, buf.psb, 1};
   if (a.p) A = TcOperand{a.p, 3, M, K, a.pld, 0, a.pps, 1};
   else RET(to_planes_f32(a.f, a.rv, a.kv, 0, M, K, 1, buf.pa, ld, 0, 3, buf.psa, st));
+  // a Gram (the same FP32 view on both sides) converts its operand once
+  const bool same = !a.p && !b.p && a.f == b.f && M == N && !memcmp(&a.rv, &b.rv, sizeof(Idx3)) &&
+                    !memcmp(&a.kv, &b.kv, sizeof(Idx3));
   if (b.p) B = TcOperand{b.p, 3, N, K, b.pld, 0, b.pps, 1};
+  else if (same) B = A;
   else RET(to_planes_f32(b.f, b.rv, b.kv, 0, N, K, 1, buf.pb, ld, 0, 3, buf.psb, st));
   TcOutput o;
   memset(&o, 0, sizeof o);

@@ -979,12 +979,17 @@ __global__ void __launch_bounds__(CQ_SOLVE_NT)
             }
           }
         }
-        // inside the block
+        // inside the block (1 / L_jj read before the chain: a load inside it,
+        // one per step, put the memory latency on the chain 32 times)
+        const float lij = (j < k) ? linv[j] : 0.f;
         float xj = 0.f;
-        for (int t = 0; t < 32 && qb * 32 + t < k; ++t) {
-          if (lane == t) xj = s * linv[j];
-          const float xt = __shfl_sync(0xffffffffu, xj, t);
-          if (lane > t && j < k) s = fmaf(-xt, Ls[pk(j, qb * 32 + t)], s);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          if (qb * 32 + t < k) {
+            if (lane == t) xj = s * lij;
+            const float xt = __shfl_sync(0xffffffffu, xj, t);
+            if (lane > t && j < k) s = fmaf(-xt, Ls[pk(j, qb * 32 + t)], s);
+          }
         }
         x[qb] = xj;
         if (j < k) U[(long long)r * ldu + j] = xj;

@@ -92,3 +92,16 @@ def test_hamiltonian_builder_is_the_xxz_chain(lib):
         dims, sites = xxz_chain(L, 1.0, D)
         assert dims[0] == dims[-1] == 1 and all(d == 5 for d in dims[1:-1])
         assert np.abs(oh.mpo_to_dense(sites) - oh.dense_xxz(L, 1.0, D)).max() < 1e-14
+
+
+def test_context_calls_reject_a_null_context(lib):
+    """Every entry point that takes a context returns XTRG_EINVAL for NULL
+    before touching the device (the switches, the state and stats calls)."""
+    L = lib.LIB
+    assert L.xtrg_set_graphs(None, 1) == lib.XTRG_EINVAL
+    assert L.xtrg_set_herm_check(None, 0) == lib.XTRG_EINVAL
+    assert L.xtrg_set_profiling(None, 1) == lib.XTRG_EINVAL
+    assert L.xtrg_init(None) == lib.XTRG_EINVAL
+    assert L.xtrg_double(None) == lib.XTRG_EINVAL
+    st = lib.xtrg_stats()
+    assert L.xtrg_get_stats(None, ctypes.byref(st)) == lib.XTRG_EINVAL

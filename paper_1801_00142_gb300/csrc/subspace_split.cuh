@@ -34,6 +34,7 @@ struct SubspaceBuffers {
   int* chol_flag;         // [0] breakdown flag of the current call, [1] count of breakdowns,
                           // [2] full second pass flag, [3] its count, [4] deflated columns
   int orth_block;         // column-block width of the orthonormalisation (32..SUBSPACE_BLOCK_K)
+  unsigned long long* seed_base;   // device counter mixed into the noise seeds (one per product)
   float* part;            // FP32 split-K partials of the small tensor-core products (may be
   size_t part_floats;     // shared with other split-K users: free during a split)
 };
@@ -77,3 +78,6 @@ cudaError_t subspace_split(const double* CE, int m, int n, int k, int dir_right,
                            unsigned long long seed, const SubspaceBuffers& b, cudaStream_t st,
                            double* disc_max, double thresh);
 const double* subspace_defect(const SubspaceBuffers& b);
+// Advance the device seed counter (once per product, inside a captured graph
+// too, so that every doubling draws fresh noise).
+cudaError_t subspace_next_seed(const SubspaceBuffers& b, cudaStream_t st);

@@ -918,6 +918,7 @@ xtrg_status compress_mixed(xtrg_ctx* ctx, DevMpo& C, int dstar, int sweeps) {
   // the end of the product
   CKM(cudaMemsetAsync(ctx->m.err, 0, sizeof(int), ctx->st));
   CKM(cudaMemsetAsync(ctx->m.acc + 3, 0, sizeof(double), ctx->st));
+  CKM(subspace_next_seed(ctx->m.sb, ctx->st));
   TRY(mixed_unit_env(ctx, 0));
   TRY(mixed_unit_env(ctx, L));
   for (int j = L - 1; j >= 1; --j) {
@@ -1221,6 +1222,7 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
       ctx->m.sb.orth_block = cfg->orth_block ? cfg->orth_block : SUBSPACE_BLOCK_K;
       // C_E's split-K partials are consumed before the split starts
       ctx->m.sb.part = ctx->m.part;
+      ctx->m.sb.seed_base = reinterpret_cast<unsigned long long*>(ctx->m.acc + 4);
       ctx->m.sb.part_floats = p.m_part;
       ok = ok && ctx->m.sb.ce_rm && ctx->m.sb.ce_tr && ctx->m.sb.ce_ss && ctx->m.sb.chol_L &&
            ctx->m.sb.chol_d && ctx->m.sb.chol_li && ctx->m.sb.chol_flag;
@@ -1237,7 +1239,7 @@ extern "C" xtrg_status xtrg_create(xtrg_ctx** out, const xtrg_mpo* Hm, const xtr
   ctx->env.resize(ctx->L + 1);
   for (int i = 0; i <= ctx->L; ++i) ctx->env[i] = envbase + (size_t)i * p.n_env;
   if (ctx->mixed_ready) {
-    const double acc0[4] = {0.0, 0.0, INFINITY, 0.0};
+    const double acc0[8] = {0.0, 0.0, INFINITY, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (cudaMemsetAsync(ctx->m.sb.chol_flag, 0, 32, ctx->st) != cudaSuccess ||
         cudaMemcpyAsync(ctx->m.acc, acc0, sizeof acc0, cudaMemcpyHostToDevice, ctx->st) !=
             cudaSuccess) {
